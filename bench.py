@@ -1,0 +1,362 @@
+"""Benchmark of the PRS hot path on GB300: site-updates/s and the HBM roofline fraction.
+
+One benchmark step = one output interval of the paper's runs: ``--interval`` (20)
+leapfrog steps (Eqs. 3-6) followed by the wall diagnostics (Eq. 7, Eq. 8) reduced in
+FP64 and read back on the host.  Default workload: 3D 1024^3 FP32, PRS (alpha=3,
+beta=0), radiation era, deta=0.1, seeded uniform(-1,1) initial field.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 3d1024|2d4096|3d512]
+       python bench.py --impl reference ...   (the FP64 oracle on the host cores)
+Under torchrun each rank runs an independent replica (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (shape, fused-steps-per-pass default, description)
+    "3d1024": ((1024, 1024, 1024), "3D 1024^3 FP32 PRS step (7-point), radiation era, deta=0.1, "
+                                   "20 steps + FP64 wall diagnostics per output"),
+    "3d512": ((512, 512, 512), "3D 512^3 FP32 PRS step, radiation era, 20 steps + FP64 wall diagnostics"),
+    "2d4096": ((4096, 4096), "2D 4096^2 FP32 PRS step (5-point), radiation era, 20 steps + FP64 wall diagnostics"),
+}
+BYTES_PER_SITE_UPDATE = {0: 16, 1: 32}  # read+write of phi and dphi (FP32, FP64)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="3d1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--interval", type=int, default=20, help="leapfrog steps per diagnostic output")
+    ap.add_argument("--tblock", type=int, default=0, help="fused steps per HBM pass (0: library default)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------- distributed
+
+def dist_setup(gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if os.environ.get("PRS_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- oracle
+
+def oracle_sample(interval: int, shape=(64, 64, 64)):
+    """One bounded step of the oracle: ``interval`` FP64 leapfrog steps + diagnostics on ``shape``."""
+    import oracle
+
+    p = oracle.Params(shape)
+    phi, v = oracle.init_random(p, 0)
+    t0 = time.perf_counter()
+    phi, v = oracle.step(p, phi, v, interval)
+    oracle.measure(p, phi, v)
+    dt = time.perf_counter() - t0
+    return p.sites * interval, dt
+
+
+def cpu_baseline(interval: int) -> dict:
+    """The oracle as it stands, single-threaded on this host: 128^3, two output intervals."""
+    shape = (128, 128, 128)
+    units, secs = 0, 0.0
+    for _ in range(2):
+        u, s = oracle_sample(interval, shape)
+        units += u
+        secs += s
+    return {"value": units / secs, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, 3D 128^3, 2 x ({interval} leapfrog steps + diagnostics), "
+                      f"{secs:.1f} s on {os.cpu_count()} host cores (1 used)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    shape = (64, 64, 64)
+    for _ in range(args.warmup):
+        oracle_sample(args.interval, shape)
+    units, secs = 0, 0.0
+    for _ in range(args.steps):
+        u, s = oracle_sample(args.interval, shape)
+        units += u
+        secs += s
+    value = units / secs
+    line = {
+        "impl": "reference", "metric": "PRS site-updates/s (FP64 oracle on host cores)", "value": value,
+        "unit": "site-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][1], "reference_sample": "3D 64^3 FP64 oracle per step",
+                   "interval": args.interval},
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"3D 64^3, {args.interval} leapfrog steps + diagnostics per step"},
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- GPU arm
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sources_sha() -> str:
+    csrc = os.path.join(ROOT, "paper_1710_10420_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(workload: str):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("sources_sha") != kernel_sources_sha():
+        return None
+    return rec
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import paper_1710_10420_gb300 as prs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prs.load(build=False)
+    shape, desc = WORKLOADS[args.workload]
+    sites = int(np.prod(shape))
+    stream = torch.cuda.Stream(dev)
+    sim = prs.Sim(shape, precision=prs.PRS_FP32, stream=stream, device=dev, seed=1000 + rank, tblock=args.tblock)
+    sim.init()
+    lib = prs.load()
+    tb = args.tblock if args.tblock > 0 else lib_default_tblock(prs, shape)
+    passes = [tb] * (args.interval // tb) + ([args.interval % tb] if args.interval % tb else [])
+
+    def one_step(events=None):
+        for t in passes:
+            if events is not None:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                prs.prs_step(sim.handle, t)
+                b.record(stream)
+                events.append((a, b, t))
+            else:
+                prs.prs_step(sim.handle, t)
+        return prs.prs_measure_ex(sim.handle)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    events = []
+    with ClockSampler(local) as clk:
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for _ in range(args.steps):
+            d = one_step(events)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    ms = start.elapsed_time(stop)
+    ms_max = allreduce_max(ms, world, dev)
+    launch_ms = [a.elapsed_time(b) for a, b, t in events if t == tb]
+    launch_avg_ms = sum(launch_ms) / len(launch_ms)
+    site_updates = sites * args.interval * args.steps * world
+    value = site_updates / (ms_max / 1e3)
+
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_SITE_UPDATE[0] * sites * tb / (launch_avg_ms / 1e3) / 1e9
+    rec = traffic_record(args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (rec["dram_bytes_per_launch"] if rec else None),
+                "kernel": f"fused PRS step, {tb} leapfrog step(s) per pass",
+                "algorithmic_bytes_per_launch": BYTES_PER_SITE_UPDATE[0] * sites * tb,
+                "launch_ms": launch_avg_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+    if rec:
+        roofline["dram_frac"] = rec["dram_bytes_per_launch"] / (launch_avg_ms / 1e3) / 1e9 / peak
+
+    e2e = run_e2e(args, prs, sim, shape, stream, dev, world)
+    clocks = clk.summary()
+    line = {
+        "metric": "PRS site-updates/s (FP32) and % HBM roofline", "value": value, "unit": "site-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "shape": list(shape), "interval": args.interval, "fused_steps_per_pass": tb,
+                   "l2": "inputs larger than L2 (state 12 GB)" if sites >= 512 ** 3 else
+                   "state comparable to L2; not flushed", "parallelism": f"replicas x{world}",
+                   "last_output": {"area_per_volume": d.area_per_volume, "gamma_v": d.gamma_v, "step": d.step}},
+        "roofline": roofline, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": args.steps * (len(passes) + 1),
+    }
+    sim.close()
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.interval)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def lib_default_tblock(prs, shape) -> int:
+    """Steps the library fuses per pass by default for this box (FP32)."""
+    return prs.prs_default_tblock(prs.make_params(shape))
+
+
+def run_e2e(args, prs, sim, shape, stream, dev, world) -> dict:
+    """Same metric through the C ABI with host buffers: upload the state, step, read the diagnostics."""
+    import torch
+
+    fshape = tuple(reversed(shape))
+    h_phi = torch.empty(fshape, dtype=torch.float32, pin_memory=True)
+    h_v = torch.empty(fshape, dtype=torch.float32, pin_memory=True)
+    n = prs.prs_get_state(sim.handle, h_phi.numpy(), h_v.numpy())
+    sites = int(np.prod(shape))
+    k = max(1, args.e2e_steps)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(k):
+        prs.prs_set_state(sim.handle, h_phi.numpy(), h_v.numpy(), n)
+        prs.prs_step(sim.handle, args.interval)
+        prs.prs_measure_ex(sim.handle)
+    torch.cuda.synchronize(dev)
+    secs = allreduce_max(time.perf_counter() - t0, world, dev)
+    return {"value": sites * args.interval * k * world / secs, "unit": "site-updates/s",
+            "h2d_bytes_per_step": 2 * sites * 4, "d2h_bytes_per_step": 48, "steps": k,
+            "path": "prs_set_state(host) + prs_step + prs_measure"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

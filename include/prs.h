@@ -1,0 +1,170 @@
+/*
+ * prs.h -- C ABI of libprs: the Press-Ryden-Spergel (PRS) domain-wall evolution of
+ * Correia & Martins, arXiv:1710.10420, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method (Sec. II of the paper):
+ *   Eq. 2  phi'' + alpha (dln a/dln eta) phi'/eta - lap phi = -a^beta dV/dphi,
+ *          V(phi) = V0 (phi^2/phi0^2 - 1)^2 (Eq. 1); PRS takes alpha = 3, beta = 0.
+ *   Eq. 3  lap phi: nearest-neighbour second difference on a periodic lattice
+ *          (5-point in 2D, 7-point in 3D), divided by dx^2.
+ *   Eq. 4  dphi^{n+1/2} = [(1-delta) dphi^{n-1/2} + deta (lap phi^n - a^beta dV/dphi^n)]/(1+delta)
+ *   Eq. 5  phi^{n+1}    = phi^n + deta dphi^{n+1/2}
+ *   Eq. 6  delta_n = alpha deta (dln a/dln eta) / (2 eta_n),  eta_n = eta0 + n deta
+ *   Eq. 7  A/V = dA sum_links delta_pm |grad phi|/(|phi,x|+|phi,y|+|phi,z|) / V
+ *   Eq. 8  (gamma v)^2 = (1/2N) sum_{wall sites} dphi^2 / V(phi)
+ *
+ * Conventions for every call:
+ *   - Every entry point returns a status code (PRS_OK = 0, negative on error) and
+ *     never throws or aborts; prs_strerror() names the code.  On error, output
+ *     arguments are left unchanged unless stated otherwise.
+ *   - Fields are structure-of-arrays: phi and dphi (= d phi / d eta) each hold
+ *     nx*ny*nz values, row-major with x fastest: idx = x + nx*(y + ny*z).
+ *     Element type is float (PRS_FP32) or double (PRS_FP64).
+ *   - "Host" pointers are ordinary CPU memory (pinned or pageable); "device"
+ *     pointers are CUDA global memory of the current device.
+ *   - Work is queued on the stream given at creation (NULL = the legacy default
+ *     stream).  Calls that return host results synchronise that stream.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef PRS_H
+#define PRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status codes */
+#define PRS_OK 0
+#define PRS_EINVAL (-1)     /* bad argument: shape, CFL, precision, NULL handle ... */
+#define PRS_ENOMEM (-2)     /* device or host allocation failed                     */
+#define PRS_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed          */
+#define PRS_ETIMEOUT (-4)   /* a bounded device-side wait gave up                    */
+#define PRS_ENONFINITE (-5) /* a diagnostic found non-finite phi or dphi            */
+#define PRS_ESTATE (-6)     /* call out of order (e.g. measuring before prs_init)   */
+
+/* ---------------------------------------------------------------- precision */
+#define PRS_FP32 0 /* float storage and arithmetic; FP64 diagnostic sums           */
+#define PRS_FP64 1 /* double storage and arithmetic                                 */
+
+/* ---------------------------------------------------------------- flags */
+/* FP64 only: evaluate each site in the canonical order with no fused multiply-add,
+ * so that fields are bit-identical to a sequential IEEE-754 double evaluation of
+ * Eqs. 3-5; the diagnostic sums are reduced in a fixed order in every mode. */
+#define PRS_REPRO 1u
+
+/* Observables of prs_adjoint (not in the paper: smooth stand-ins for Eq. 7). */
+#define PRS_OBS_GRAD_ENERGY 0 /* J = 1/2 sum_s sum_d ((phi_{s+e_d} - phi_s)/dx)^2            */
+#define PRS_OBS_SMOOTH_AREA 1 /* J = 1/(S dx) sum_links (1 - tanh(phi_s/eps) tanh(phi_t/eps))/2 */
+
+typedef struct prs_sim prs_sim;     /* one lattice run; opaque, owned by the library */
+typedef struct prs_batch prs_batch; /* an ensemble of independent runs              */
+
+/* Parameters of one run (Eq. 2, Eq. 6, and the lattice).  Configs of the paper's
+ * kind use dx = 1, deta = 0.1, eta0 = 1, alpha = 3, beta = 0, phi0 = 1, W0 = 10. */
+typedef struct {
+    int32_t dims;      /* 2 or 3                                                    */
+    int32_t precision; /* PRS_FP32 or PRS_FP64                                      */
+    int64_t N;         /* box side along x (and along y, z unless Ny, Nz are set); >= 3 */
+    int64_t Ny, Nz;    /* sides along y and z; 0 means N.  Nz is ignored in 2D       */
+    double dx;         /* lattice spacing (> 0)                                     */
+    double deta;       /* conformal time step (> 0)                                 */
+    double eta0;       /* conformal time of step 0 (> 0)                            */
+    double alpha;      /* damping coefficient of Eq. 2 (PRS: 3)                     */
+    double beta;       /* force exponent of a^beta (PRS: 0); a(eta) = eta^era_m     */
+    double era_m;      /* dln a / dln eta: 1 radiation, 2 matter                    */
+    double W0;         /* wall thickness: V0 = pi^2/(2 W0^2); +inf gives V0 = 0     */
+    double phi0;       /* vacuum value (> 0)                                        */
+    uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
+    uint32_t flags;    /* PRS_REPRO or 0                                            */
+    int32_t tblock;    /* leapfrog steps fused per pass over HBM; 0 = library picks */
+} prs_params;
+
+/* One output record of the wall diagnostics (Eq. 7, Eq. 8). */
+typedef struct {
+    double area_per_volume; /* A/V of Eq. 7, dA = dx^(D-1), V = sites * dx^D          */
+    double gamma_v;         /* sqrt of Eq. 8; 0 when there is no wall site            */
+    double sum_w;           /* sum over crossing links of |g|/sum_i|g_i|              */
+    double sum_ratio;       /* sum over wall sites (V > 0) of dphi^2 / V(phi)         */
+    int64_t n_links;        /* links (s, s+e_d) with (phi_s < 0) != (phi_t < 0)       */
+    int64_t n_wall;         /* sites with a nearest neighbour of the opposite sign    */
+    int64_t n_vzero;        /* wall sites with V(phi) == 0, left out of Eq. 8         */
+    int64_t n_nonfinite;    /* sites where phi or dphi is NaN or infinite             */
+    int64_t step;           /* n: the field measured is phi^n, dphi^{n-1/2}           */
+    double eta;             /* eta_n = eta0 + n deta                                  */
+} prs_diag;
+
+/* ------------------------------------------------------------ single runs */
+
+/* Create a run.  Validates the parameters, including the leapfrog stability
+ * limit deta^2 (4 D/dx^2 + max|V''|) < 4 (Eqs. 3-5), and allocates the small
+ * device scratch used by the diagnostics.  Field buffers are allocated on the
+ * first prs_init/prs_set_state unless prs_bind supplies them.
+ * stream: a cudaStream_t, or NULL.  *out receives the handle. */
+int prs_create(const prs_params* params, void* stream, prs_sim** out);
+
+/* Use caller-owned device buffers for the fields instead of library memory.
+ * d_phi_a and d_phi_b each hold one field (the leapfrog writes phi^{n+1} into the
+ * buffer that does not hold phi^n); d_dphi holds dphi and is updated in place.
+ * Each must be 16-byte aligned and hold sites * element-size bytes; they stay
+ * owned by the caller and must outlive the run.  Must precede prs_init. */
+int prs_bind(prs_sim* sim, void* d_phi_a, void* d_phi_b, void* d_dphi);
+
+/* Set the initial state (step 0).  h_phi == NULL: phi_s is drawn on the device
+ * from SplitMix64 (Steele, Lea & Flood 2014) at counter idx+1 after params.seed,
+ * top 24 bits k, phi = (2k+1) 2^-24 - 1: i.i.d. uniform in (-1,1), exact in FP32
+ * (the paper's random initial conditions, Sec. III).  h_dphi == NULL: dphi = 0
+ * (the first kick starts from dphi^{-1/2} = dphi_init).  Host arrays are copied. */
+int prs_init(prs_sim* sim, const void* h_phi, const void* h_dphi);
+
+/* Queue nsteps (>= 0) leapfrog steps (Eqs. 3-6) on the run's stream; returns
+ * without waiting.  Step n uses delta_n, eta_n = eta0 + n deta. */
+int prs_step(prs_sim* sim, int64_t nsteps);
+
+/* Wall diagnostics of the current state (Eq. 7, Eq. 8), reduced on the device in
+ * FP64 in a fixed order, then copied to the host; synchronises the stream.
+ * Any output pointer may be NULL.  Returns PRS_ENONFINITE (outputs still written)
+ * when some phi or dphi is not finite. */
+int prs_measure(prs_sim* sim, double* area_per_volume, double* gamma_v, int64_t* n_links,
+                int64_t* n_wall_sites);
+
+/* As prs_measure, filling the whole record. */
+int prs_measure_ex(prs_sim* sim, prs_diag* out);
+
+/* Checkpoint: copy the current fields to host arrays (either may be NULL) and the
+ * step index to *n (may be NULL).  Synchronises. */
+int prs_get_state(prs_sim* sim, void* h_phi, void* h_dphi, int64_t* n);
+
+/* Resume: overwrite the fields from host arrays (both required) and set the step
+ * index (>= 0).  Bit-exact round trip with prs_get_state. */
+int prs_set_state(prs_sim* sim, const void* h_phi, const void* h_dphi, int64_t n);
+
+/* Device pointers of the current fields and the step index (any output may be
+ * NULL).  The pointers stay valid until the next prs_step or prs_destroy. */
+int prs_device_state(prs_sim* sim, void** d_phi, void** d_dphi, int64_t* n);
+
+/* Release the run and the memory the library allocated for it (not bound buffers). */
+int prs_destroy(prs_sim* sim);
+
+/* Step-n coefficients as the library computes them on the host in FP64:
+ * out[0] = c1 = (1-delta_n)/(1+delta_n), out[1] = c2 = deta/(1+delta_n) (Eq. 4, 6),
+ * out[2] = cV = 4 V0 a_n^beta / phi0^2 (force prefactor), out[3] = delta_n,
+ * out[4] = d delta_n / d alpha. */
+int prs_coefficients(const prs_params* params, int64_t n, double out[5]);
+
+/* Leapfrog steps the library fuses into one pass over HBM for these parameters
+ * when params->tblock is 0 (>= 1), or a negative status for invalid parameters. */
+int prs_default_tblock(const prs_params* params);
+
+/* Human-readable name of a status code (static string). */
+const char* prs_strerror(int status);
+
+/* Last CUDA error text seen by the library on this thread (static buffer). */
+const char* prs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRS_H */

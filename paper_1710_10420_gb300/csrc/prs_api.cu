@@ -1,0 +1,373 @@
+// prs_api.cu -- the C ABI of include/prs.h for single runs: parameter checks, the
+// FP64 damping schedule (Eq. 6), buffer ownership, and the order of kernel launches.
+// No exception crosses the ABI; every CUDA error becomes PRS_ECUDA.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "prs.h"
+#include "prs_internal.h"
+
+using namespace prs;
+
+struct prs_sim {
+    prs_params p;
+    Geo g;
+    size_t elem;         // bytes per value
+    cudaStream_t stream;
+    void* phi[2];        // ping-pong field buffers
+    void* dphi;          // velocity, updated in place
+    int cur;             // which phi[] holds phi^n
+    bool owned;          // library allocated phi[] and dphi
+    bool have_buffers;
+    bool initialised;
+    int64_t n;           // step index of the state
+    double rc[6];        // deta, 1/dx^2, 1/phi0^2, 2D, V0, phi0
+    DiagScratch scr;
+    DiagAcc* h_result;   // pinned
+};
+
+// ------------------------------------------------------------------ errors
+
+static thread_local char g_last_error[256] = "";
+
+static int cuda_fail(cudaError_t e, const char* what)
+{
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
+    return PRS_ECUDA;
+}
+
+#define PRS_CUDA(call)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+extern "C" const char* prs_strerror(int status)
+{
+    switch (status) {
+        case PRS_OK: return "ok";
+        case PRS_EINVAL: return "invalid argument";
+        case PRS_ENOMEM: return "out of memory";
+        case PRS_ECUDA: return "CUDA error";
+        case PRS_ETIMEOUT: return "device wait timed out";
+        case PRS_ENONFINITE: return "non-finite field value";
+        case PRS_ESTATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* prs_last_error(void) { return g_last_error; }
+
+// ------------------------------------------------------------- parameters
+
+static const double kPi = 3.14159265358979323846;
+
+static double potential_height(const prs_params& p) { return kPi * kPi / (2.0 * p.W0 * p.W0); }
+
+// Eq. 6 and the force prefactor of Eq. 2 at step n, in FP64 on the host.
+static void step_coefficients(const prs_params& p, int64_t n, double out[5])
+{
+    double eta = p.eta0 + (double)n * p.deta;  // computed from n, never accumulated
+    double delta = 0.5 * p.alpha * p.deta * p.era_m / eta;
+    double a_beta = 1.0;
+    if (p.beta != 0.0) a_beta = pow(pow(eta, p.era_m), p.beta);  // a = eta^m, a(1) = 1
+    out[0] = (1.0 - delta) / (1.0 + delta);
+    out[1] = p.deta / (1.0 + delta);
+    out[2] = 4.0 * potential_height(p) * a_beta / (p.phi0 * p.phi0);
+    out[3] = delta;
+    out[4] = 0.5 * p.deta * p.era_m / eta;
+}
+
+// Leapfrog stability of Eqs. 3-5 at step n: deta^2 (4D/dx^2 + max|V''|)/4 < 1,
+// with max|V''| = 2 cV over |phi| <= phi0.
+static bool cfl_ok(const prs_params& p, int64_t n)
+{
+    double c[5];
+    step_coefficients(p, n, c);
+    double lam = 4.0 * p.dims / (p.dx * p.dx) + 2.0 * c[2] * p.phi0 * p.phi0;
+    return p.deta * p.deta * lam < 4.0;
+}
+
+static int check_params(const prs_params* pp, Geo* g)
+{
+    if (!pp) return PRS_EINVAL;
+    const prs_params& p = *pp;
+    if (p.dims != 2 && p.dims != 3) return PRS_EINVAL;
+    if (p.precision != PRS_FP32 && p.precision != PRS_FP64) return PRS_EINVAL;
+    if ((p.flags & ~PRS_REPRO) != 0) return PRS_EINVAL;
+    int64_t nx = p.N, ny = p.Ny ? p.Ny : p.N, nz = p.dims == 3 ? (p.Nz ? p.Nz : p.N) : 1;
+    if (nx < 3 || ny < 3 || (p.dims == 3 && nz < 3)) return PRS_EINVAL;
+    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30)) return PRS_EINVAL;
+    if (!(p.dx > 0) || !(p.deta > 0) || !(p.eta0 > 0) || !(p.phi0 > 0) || !(p.W0 > 0)) return PRS_EINVAL;
+    if (!isfinite(p.dx) || !isfinite(p.deta) || !isfinite(p.eta0) || !isfinite(p.phi0)) return PRS_EINVAL;
+    if (!isfinite(p.alpha) || !isfinite(p.beta) || !isfinite(p.era_m)) return PRS_EINVAL;
+    if (p.tblock < 0 || p.tblock > 8) return PRS_EINVAL;
+    if (!cfl_ok(p, 0)) return PRS_EINVAL;
+    // delta must stay below 1 or (1-delta)/(1+delta) flips the velocity's sign
+    double c[5];
+    step_coefficients(p, 0, c);
+    if (!(c[3] < 1.0)) return PRS_EINVAL;
+    g->dims = p.dims;
+    g->nx = (int)nx;
+    g->ny = (int)ny;
+    g->nz = (int)nz;
+    g->S = nx * ny * nz;
+    return PRS_OK;
+}
+
+extern "C" int prs_coefficients(const prs_params* params, int64_t n, double out[5])
+{
+    if (!params || !out || n < 0) return PRS_EINVAL;
+    step_coefficients(*params, n, out);
+    return PRS_OK;
+}
+
+extern "C" int prs_default_tblock(const prs_params* params)
+{
+    Geo g;
+    int rc = check_params(params, &g);
+    if (rc) return rc;
+    int t = max_fused_steps(g, params->precision, (params->flags & PRS_REPRO) != 0);
+    return t < 1 ? 1 : t;
+}
+
+// -------------------------------------------------------------- lifecycle
+
+static const int kMeasureBlocks = 152 * 8;
+
+extern "C" int prs_create(const prs_params* params, void* stream, prs_sim** out)
+{
+    if (!out) return PRS_EINVAL;
+    Geo g;
+    int rc = check_params(params, &g);
+    if (rc) return rc;
+    prs_sim* s = new (std::nothrow) prs_sim();
+    if (!s) return PRS_ENOMEM;
+    s->p = *params;
+    s->g = g;
+    s->elem = params->precision == PRS_FP32 ? sizeof(float) : sizeof(double);
+    s->stream = (cudaStream_t)stream;
+    s->rc[0] = params->deta;
+    s->rc[1] = 1.0 / (params->dx * params->dx);
+    s->rc[2] = 1.0 / (params->phi0 * params->phi0);
+    s->rc[3] = (double)(2 * params->dims);
+    s->rc[4] = potential_height(*params);
+    s->rc[5] = params->phi0;
+    s->scr.max_blocks = kMeasureBlocks;
+    void* blob = nullptr;
+    size_t bytes = sizeof(DiagAcc) * (kMeasureBlocks + 1) + 256;
+    if (cudaMalloc(&blob, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return PRS_ENOMEM;
+    }
+    s->scr.partials = (DiagAcc*)blob;
+    s->scr.result = s->scr.partials + kMeasureBlocks;
+    s->scr.counter = (unsigned int*)((char*)blob + sizeof(DiagAcc) * (kMeasureBlocks + 1));
+    if (cudaMemset(blob, 0, bytes) != cudaSuccess || cudaMallocHost((void**)&s->h_result, sizeof(DiagAcc)) != cudaSuccess) {
+        int r = cuda_fail(cudaGetLastError(), "prs_create");
+        cudaFree(blob);
+        delete s;
+        return r;
+    }
+    *out = s;
+    return PRS_OK;
+}
+
+extern "C" int prs_bind(prs_sim* s, void* d_phi_a, void* d_phi_b, void* d_dphi)
+{
+    if (!s || !d_phi_a || !d_phi_b || !d_dphi || d_phi_a == d_phi_b) return PRS_EINVAL;
+    if (((uintptr_t)d_phi_a | (uintptr_t)d_phi_b | (uintptr_t)d_dphi) & 15u) return PRS_EINVAL;
+    if (s->have_buffers) return PRS_ESTATE;
+    s->phi[0] = d_phi_a;
+    s->phi[1] = d_phi_b;
+    s->dphi = d_dphi;
+    s->cur = 0;
+    s->owned = false;
+    s->have_buffers = true;
+    return PRS_OK;
+}
+
+static int ensure_buffers(prs_sim* s)
+{
+    if (s->have_buffers) return PRS_OK;
+    size_t bytes = (size_t)s->g.S * s->elem;
+    void *a = nullptr, *b = nullptr, *v = nullptr;
+    if (cudaMalloc(&a, bytes) != cudaSuccess || cudaMalloc(&b, bytes) != cudaSuccess ||
+        cudaMalloc(&v, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(a);
+        cudaFree(b);
+        cudaFree(v);
+        return PRS_ENOMEM;
+    }
+    s->phi[0] = a;
+    s->phi[1] = b;
+    s->dphi = v;
+    s->cur = 0;
+    s->owned = true;
+    s->have_buffers = true;
+    return PRS_OK;
+}
+
+extern "C" int prs_destroy(prs_sim* s)
+{
+    if (!s) return PRS_EINVAL;
+    cudaStreamSynchronize(s->stream);
+    if (s->owned) {
+        cudaFree(s->phi[0]);
+        cudaFree(s->phi[1]);
+        cudaFree(s->dphi);
+    }
+    cudaFree(s->scr.partials);
+    cudaFreeHost(s->h_result);
+    delete s;
+    return PRS_OK;
+}
+
+// ------------------------------------------------------------------ state
+
+extern "C" int prs_init(prs_sim* s, const void* h_phi, const void* h_dphi)
+{
+    if (!s) return PRS_EINVAL;
+    int rc = ensure_buffers(s);
+    if (rc) return rc;
+    size_t bytes = (size_t)s->g.S * s->elem;
+    s->cur = 0;
+    if (h_phi) {
+        PRS_CUDA(cudaMemcpyAsync(s->phi[0], h_phi, bytes, cudaMemcpyHostToDevice, s->stream));
+        if (h_dphi)
+            PRS_CUDA(cudaMemcpyAsync(s->dphi, h_dphi, bytes, cudaMemcpyHostToDevice, s->stream));
+        else
+            PRS_CUDA(cudaMemsetAsync(s->dphi, 0, bytes, s->stream));
+    } else {
+        PRS_CUDA(launch_init_random(s->g, s->p.precision, s->p.seed, s->phi[0], s->dphi, h_dphi == nullptr,
+                                    s->stream));
+        if (h_dphi) PRS_CUDA(cudaMemcpyAsync(s->dphi, h_dphi, bytes, cudaMemcpyHostToDevice, s->stream));
+    }
+    // host arrays may be pageable and reused by the caller right after return
+    PRS_CUDA(cudaStreamSynchronize(s->stream));
+    s->n = 0;
+    s->initialised = true;
+    return PRS_OK;
+}
+
+extern "C" int prs_set_state(prs_sim* s, const void* h_phi, const void* h_dphi, int64_t n)
+{
+    if (!s || !h_phi || !h_dphi || n < 0) return PRS_EINVAL;
+    int rc = ensure_buffers(s);
+    if (rc) return rc;
+    size_t bytes = (size_t)s->g.S * s->elem;
+    PRS_CUDA(cudaMemcpyAsync(s->phi[s->cur], h_phi, bytes, cudaMemcpyHostToDevice, s->stream));
+    PRS_CUDA(cudaMemcpyAsync(s->dphi, h_dphi, bytes, cudaMemcpyHostToDevice, s->stream));
+    PRS_CUDA(cudaStreamSynchronize(s->stream));
+    s->n = n;
+    s->initialised = true;
+    return PRS_OK;
+}
+
+extern "C" int prs_get_state(prs_sim* s, void* h_phi, void* h_dphi, int64_t* n)
+{
+    if (!s) return PRS_EINVAL;
+    if (!s->initialised) return PRS_ESTATE;
+    size_t bytes = (size_t)s->g.S * s->elem;
+    if (h_phi) PRS_CUDA(cudaMemcpyAsync(h_phi, s->phi[s->cur], bytes, cudaMemcpyDeviceToHost, s->stream));
+    if (h_dphi) PRS_CUDA(cudaMemcpyAsync(h_dphi, s->dphi, bytes, cudaMemcpyDeviceToHost, s->stream));
+    PRS_CUDA(cudaStreamSynchronize(s->stream));
+    if (n) *n = s->n;
+    return PRS_OK;
+}
+
+extern "C" int prs_device_state(prs_sim* s, void** d_phi, void** d_dphi, int64_t* n)
+{
+    if (!s) return PRS_EINVAL;
+    if (!s->initialised) return PRS_ESTATE;
+    if (d_phi) *d_phi = s->phi[s->cur];
+    if (d_dphi) *d_dphi = s->dphi;
+    if (n) *n = s->n;
+    return PRS_OK;
+}
+
+// ------------------------------------------------------------------- step
+
+extern "C" int prs_step(prs_sim* s, int64_t nsteps)
+{
+    if (!s || nsteps < 0) return PRS_EINVAL;
+    if (!s->initialised) return PRS_ESTATE;
+    if (nsteps == 0) return PRS_OK;
+    if (!cfl_ok(s->p, s->n + nsteps - 1)) return PRS_EINVAL;
+    const bool repro = (s->p.flags & PRS_REPRO) != 0;
+    int tmax = max_fused_steps(s->g, s->p.precision, repro);
+    int tb = s->p.tblock > 0 ? s->p.tblock : tmax;
+    if (tb > tmax) tb = tmax;
+    if (tb < 1) tb = 1;
+    double c1[8], c2[8], cV[8];
+    int64_t done = 0;
+    while (done < nsteps) {
+        int t = (int)((nsteps - done) < tb ? (nsteps - done) : tb);
+        for (int k = 0; k < t; ++k) {
+            double c[5];
+            step_coefficients(s->p, s->n + done + k, c);
+            c1[k] = c[0];
+            c2[k] = c[1];
+            cV[k] = c[2];
+        }
+        const void* in = s->phi[s->cur];
+        void* out = s->phi[1 - s->cur];
+        cudaError_t e = launch_step(s->g, s->p.precision, repro, in, out, s->dphi, c1, c2, cV, t, s->rc, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
+        s->cur = 1 - s->cur;
+        done += t;
+    }
+    s->n += nsteps;
+    return PRS_OK;
+}
+
+// ---------------------------------------------------------------- measure
+
+static int measure_into(prs_sim* s, prs_diag* d)
+{
+    if (!s->initialised) return PRS_ESTATE;
+    cudaError_t e = launch_measure(s->g, s->p.precision, s->phi[s->cur], s->dphi, s->rc, s->scr, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "prs_measure launch");
+    PRS_CUDA(cudaMemcpyAsync(s->h_result, s->scr.result, sizeof(DiagAcc), cudaMemcpyDeviceToHost, s->stream));
+    PRS_CUDA(cudaStreamSynchronize(s->stream));
+    const DiagAcc& a = *s->h_result;
+    d->sum_w = a.sum_w;
+    d->sum_ratio = a.sum_ratio;
+    d->n_links = a.n_links;
+    d->n_wall = a.n_wall;
+    d->n_vzero = a.n_vzero;
+    d->n_nonfinite = a.n_nonfinite;
+    d->area_per_volume = a.sum_w / ((double)s->g.S * s->p.dx);  // dA/V = dx^(D-1)/(S dx^D)
+    int64_t nw = a.n_wall - a.n_vzero;
+    d->gamma_v = nw > 0 ? sqrt(a.sum_ratio / (2.0 * (double)nw)) : 0.0;
+    d->step = s->n;
+    d->eta = s->p.eta0 + (double)s->n * s->p.deta;
+    return a.n_nonfinite ? PRS_ENONFINITE : PRS_OK;
+}
+
+extern "C" int prs_measure_ex(prs_sim* s, prs_diag* out)
+{
+    if (!s || !out) return PRS_EINVAL;
+    return measure_into(s, out);
+}
+
+extern "C" int prs_measure(prs_sim* s, double* area_per_volume, double* gamma_v, int64_t* n_links,
+                           int64_t* n_wall_sites)
+{
+    if (!s) return PRS_EINVAL;
+    prs_diag d;
+    int rc = measure_into(s, &d);
+    if (rc != PRS_OK && rc != PRS_ENONFINITE) return rc;
+    if (area_per_volume) *area_per_volume = d.area_per_volume;
+    if (gamma_v) *gamma_v = d.gamma_v;
+    if (n_links) *n_links = d.n_links;
+    if (n_wall_sites) *n_wall_sites = d.n_wall;
+    return rc;
+}

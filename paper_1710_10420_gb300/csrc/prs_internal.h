@@ -1,0 +1,70 @@
+// prs_internal.h -- shared between the host API (prs_api.cu) and the kernel files.
+// Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "prs.h"
+
+namespace prs {
+
+// Lattice geometry in the layout of the ABI: idx = x + nx*(y + ny*z), x fastest.
+struct Geo {
+    int dims;
+    int nx, ny, nz;  // nz = 1 in 2D
+    int64_t S;       // sites
+};
+
+// Per-step coefficients of Eq. 4 with Eq. 6 and the force prefactor, in working precision.
+template <typename R>
+struct StepCoef {
+    R c1, c2, cV;
+};
+
+// Scalars fixed for the whole run, in working precision.
+template <typename R>
+struct RunConst {
+    R deta;        // Eq. 5
+    R inv_dx2;     // 1/dx^2 of Eq. 3
+    R inv_phi0sq;  // 1/phi0^2
+    R twoD;        // 2*dims, the centre weight of Eq. 3
+    R V0;          // potential height (Eq. 1)
+    R phi0;        // vacuum value
+};
+
+// Device-side result of one diagnostic reduction (Eq. 7, Eq. 8 sums and counts).
+struct DiagAcc {
+    double sum_w;
+    double sum_ratio;
+    long long n_links;
+    long long n_wall;
+    long long n_vzero;
+    long long n_nonfinite;
+};
+
+// Device scratch of the diagnostics: per-block partials + a completion counter.
+struct DiagScratch {
+    DiagAcc* partials;     // [max_blocks]
+    DiagAcc* result;       // [1]
+    unsigned int* counter; // [1], zero between launches
+    int max_blocks;
+};
+
+// Kernel launchers (prs_kernels.cu).  Each returns cudaSuccess or the launch error.
+cudaError_t launch_init_random(const Geo& g, int precision, uint64_t seed, void* phi, void* dphi, bool zero_dphi,
+                               cudaStream_t st);
+
+// One pass of `nsteps_in_pass` fused leapfrog steps from phi_in into phi_out,
+// dphi in place.  coef holds one entry per fused step (host memory, by value).
+cudaError_t launch_step(const Geo& g, int precision, bool repro, const void* phi_in, void* phi_out, void* dphi,
+                        const double* c1, const double* c2, const double* cV, int nsteps_in_pass,
+                        const double run_const[6], cudaStream_t st);
+
+// Largest number of steps one launch_step pass can fuse for this geometry/precision.
+int max_fused_steps(const Geo& g, int precision, bool repro);
+
+cudaError_t launch_measure(const Geo& g, int precision, const void* phi, const void* dphi, const double run_const[6],
+                           const DiagScratch& scr, cudaStream_t st);
+
+}  // namespace prs

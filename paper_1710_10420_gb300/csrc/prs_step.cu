@@ -1,0 +1,25 @@
+// prs_step.cu -- chooses the kernel for one pass of fused leapfrog steps.
+#include "prs_internal.h"
+
+namespace prs {
+
+cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const void* in, void* out, void* dphi,
+                                double c1, double c2, double cV, const double rcd[6], cudaStream_t st);
+
+int max_fused_steps(const Geo& g, int precision, bool repro)
+{
+    (void)g;
+    (void)precision;
+    (void)repro;
+    return 1;
+}
+
+cudaError_t launch_step(const Geo& g, int precision, bool repro, const void* phi_in, void* phi_out, void* dphi,
+                        const double* c1, const double* c2, const double* cV, int nsteps_in_pass,
+                        const double run_const[6], cudaStream_t st)
+{
+    if (nsteps_in_pass != 1) return cudaErrorInvalidValue;
+    return launch_step_generic(g, precision, repro, phi_in, phi_out, dphi, c1[0], c2[0], cV[0], run_const, st);
+}
+
+}  // namespace prs

@@ -1,0 +1,73 @@
+"""The C ABI: library loads, exports every declared symbol, validates arguments (CPU only).
+
+No compute call is made here: only host-side entry points that fail before
+touching the device, and the host coefficient schedule.
+"""
+import ctypes
+import math
+
+import pytest
+
+import paper_1710_10420_gb300 as prs
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return prs.load(build=True)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = prs.declared_functions()
+    assert "prs_create" in names and "prs_step" in names and "prs_measure" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    for n in prs.declared_functions():
+        assert hasattr(prs, n), f"binding lacks {n}"
+
+
+def test_strerror(lib):
+    assert prs.strerror(prs.PRS_OK) == "ok"
+    assert prs.strerror(prs.PRS_EINVAL) == "invalid argument"
+    assert prs.strerror(12345) == "unknown status"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(shape=(2, 8)),                       # side < 3
+    dict(shape=(8, 8), deta=1.0),             # leapfrog unstable: deta^2 * 8 >= 4
+    dict(shape=(8, 8, 8), deta=0.82),         # 3D limit deta < 0.816
+    dict(shape=(8, 8), precision=7),
+    dict(shape=(8, 8), dx=0.0),
+    dict(shape=(8, 8), eta0=0.0),
+    dict(shape=(8, 8), eta0=0.1, deta=0.2),   # delta >= 1 at the first step
+    dict(shape=(8, 8), tblock=99),
+    dict(shape=(8, 8), flags=8),
+])
+def test_create_rejects_bad_parameters(lib, bad):
+    shape = bad.pop("shape")
+    p = prs.make_params(shape, **bad)
+    h = ctypes.c_void_p()
+    assert lib.prs_create(ctypes.byref(p), None, ctypes.byref(h)) == prs.PRS_EINVAL
+    assert h.value is None
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.prs_step(None, 1) == prs.PRS_EINVAL
+    assert lib.prs_measure(None, None, None, None, None) == prs.PRS_EINVAL
+    assert lib.prs_destroy(None) == prs.PRS_EINVAL
+    assert lib.prs_create(None, None, None) == prs.PRS_EINVAL
+
+
+def test_host_coefficients_follow_eq6():
+    """delta_n = alpha deta m/(2 eta_n): the paper's radiation-era PRS first step has delta = 0.15."""
+    p = prs.make_params((8, 8))
+    c = prs.prs_coefficients(p, 0)
+    assert c["delta"] == pytest.approx(0.15, rel=1e-15)
+    assert c["c1"] == pytest.approx(0.85 / 1.15, rel=1e-15)
+    assert c["c2"] == pytest.approx(0.1 / 1.15, rel=1e-15)
+    assert c["cV"] == pytest.approx(4 * math.pi ** 2 / 200, rel=1e-15)
+    c = prs.prs_coefficients(prs.make_params((8, 8), era_m=2.0), 10)  # eta = 2
+    assert c["delta"] == pytest.approx(0.5 * 3 * 0.1 * 2 / 2.0, rel=1e-15)
+    assert prs.prs_coefficients(prs.make_params((8, 8), W0=math.inf), 0)["cV"] == 0.0

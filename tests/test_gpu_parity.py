@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (written in each test):
+  * FP64 with PRS_REPRO: fields bit-identical to the oracle; link and wall counts exact;
+    A/V and gamma v within 1e-13 relative (only the order of the FP64 reduction differs).
+  * FP64 without PRS_REPRO (fused multiply-add allowed): fields within 1e-12 relative
+    after 20 steps.
+  * FP32: fields within 1e-5 relative (||d||_inf / ||phi||_inf) after 20 steps.  On one
+    given FP32 field the counts are exact and A/V, gamma v agree to 1e-5 (each site
+    weight is a few float roundings; the sums are FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1710_10420_gb300 as prs
+import prs_inputs as inp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available()
+    prs.load(build=True)
+    yield
+    torch.cuda.synchronize()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _run(shape, precision, nsteps, phi0=None, v0=None, **kw):
+    sim = prs.Sim(shape, precision=precision, **kw)
+    sim.init(phi0, v0)
+    sim.step(nsteps)
+    phi, v, n = sim.get_state()
+    sim.close()
+    assert n == nsteps
+    return phi, v
+
+
+# ------------------------------------------------------------------ init
+
+@pytest.mark.parametrize("precision", [prs.PRS_FP32, prs.PRS_FP64])
+@pytest.mark.parametrize("shape", [(17, 19), (8, 6, 5), (128, 128)])
+def test_random_initial_field_bit_exact(precision, shape):
+    sim = prs.Sim(shape, precision=precision, seed=12345)
+    sim.init()
+    phi, v, n = sim.get_state()
+    sim.close()
+    ophi, ov = oracle.init_random(oracle.Params(shape), 12345)
+    assert n == 0
+    assert np.array_equal(phi.astype(np.float64), ophi) and np.all(v == 0)
+
+
+# ----------------------------------------------------------------- steps
+
+REPRO_CASES = [((128, 128), 20), ((17, 19), 25), ((3, 3), 7), ((32, 32, 32), 20), ((9, 7, 5), 15), ((36, 4, 3), 9),
+               ((130, 66), 11)]
+
+
+@pytest.mark.parametrize("shape,nsteps", REPRO_CASES)
+def test_fp64_repro_bit_exact(shape, nsteps):
+    p = oracle.Params(shape, W0=6.0)
+    ophi, ov = oracle.init_random(p, 3)
+    ov = 0.2 * inp.random_field(shape, seed=4)
+    phi, v = _run(shape, prs.PRS_FP64, nsteps, ophi, ov, W0=6.0, flags=prs.PRS_REPRO)
+    ophi, ov = oracle.step(p, ophi, ov, nsteps)
+    assert np.array_equal(phi, ophi)
+    assert np.array_equal(v, ov)
+
+
+def test_config_128sq_fp64_full_run():
+    """2D 128^2, FP64, PRS radiation era, eta 1 -> 64 (630 steps), diagnostics every 10 steps."""
+    shape = (128, 128)
+    p = oracle.Params(shape)
+    sim = prs.Sim(shape, precision=prs.PRS_FP64, flags=prs.PRS_REPRO, seed=0)
+    sim.init()
+    phi, v = oracle.init_random(p, 0)
+    n = 0
+    while n < 630:
+        d = sim.measure()
+        od = oracle.measure(p, phi, v)
+        assert d["step"] == n
+        assert (d["n_links"], d["n_wall"], d["n_vzero"]) == (od.n_links, od.n_wall, od.n_vzero)
+        assert d["area_per_volume"] == pytest.approx(od.area_per_volume, rel=1e-13)
+        assert d["gamma_v"] == pytest.approx(od.gamma_v, rel=1e-13, abs=1e-300)
+        k = 10
+        sim.step(k)
+        phi, v = oracle.step(p, phi, v, k, n0=n)
+        n += k
+    gphi, gv, gn = sim.get_state()
+    sim.close()
+    assert gn == 630 and np.array_equal(gphi, phi) and np.array_equal(gv, v)
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (33, 31), (16, 16, 16), (12, 10, 14)])
+def test_fp64_fma_close(shape):
+    p = oracle.Params(shape, era_m=2.0)
+    ophi, ov = oracle.init_random(p, 9)
+    phi, v = _run(shape, prs.PRS_FP64, 20, ophi, ov, era_m=2.0)
+    ophi, ov = oracle.step(p, ophi, ov, 20)
+    assert _rel(phi, ophi) <= 1e-12
+    assert _rel(v, ov) <= 1e-12
+
+
+FP32_CASES = [(128, 128), (256, 64), (130, 66), (17, 19), (64, 64, 64), (32, 16, 24), (20, 12, 9), (128, 8, 8)]
+
+
+@pytest.mark.parametrize("shape", FP32_CASES)
+@pytest.mark.parametrize("era_m", [1.0, 2.0])
+def test_fp32_close(shape, era_m):
+    p = oracle.Params(shape, era_m=era_m)
+    ophi, ov = oracle.init_random(p, 21)
+    phi, v = _run(shape, prs.PRS_FP32, 20, None, None, era_m=era_m, seed=21)
+    ophi, ov = oracle.step(p, ophi, ov, 20)
+    assert _rel(phi, ophi) <= 1e-5
+    assert _rel(v, ov) <= 1e-5
+
+
+@pytest.mark.parametrize("tblock", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(256, 256), (64, 48, 40)])
+def test_fp32_temporal_blocks(shape, tblock):
+    """Every fused-steps-per-pass setting gives the same field (to FP32 rounding) as the oracle."""
+    p = oracle.Params(shape)
+    ophi, ov = oracle.init_random(p, 5)
+    phi, v = _run(shape, prs.PRS_FP32, 23, None, None, seed=5, tblock=tblock)
+    ophi, ov = oracle.step(p, ophi, ov, 23)
+    assert _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
+
+
+def test_zero_steps_and_resume_bit_exact():
+    shape = (48, 40, 8)
+    sim = prs.Sim(shape, precision=prs.PRS_FP32, seed=2)
+    sim.init()
+    sim.step(0)
+    a_phi, a_v, n = sim.get_state()
+    assert n == 0
+    sim.step(7)
+    mid_phi, mid_v, n = sim.get_state()
+    sim.step(6)
+    end_phi, end_v, n = sim.get_state()
+    assert n == 13
+    # restart from the checkpoint at step 7 in a fresh run
+    sim2 = prs.Sim(shape, precision=prs.PRS_FP32, seed=99)
+    sim2.set_state(mid_phi, mid_v, 7)
+    sim2.step(6)
+    r_phi, r_v, n2 = sim2.get_state()
+    assert n2 == 13 and np.array_equal(r_phi, end_phi) and np.array_equal(r_v, end_v)
+    sim.close()
+    sim2.close()
+
+
+def test_library_owned_buffers():
+    """Without prs_bind the library allocates the fields itself."""
+    shape = (32, 24)
+    p = prs.make_params(shape, precision=prs.PRS_FP64, flags=prs.PRS_REPRO, seed=1)
+    h = prs.prs_create(p)
+    prs.prs_init(h)
+    prs.prs_step(h, 5)
+    phi = np.empty((24, 32))
+    v = np.empty((24, 32))
+    assert prs.prs_get_state(h, phi, v) == 5
+    a, g, nl, nw = prs.prs_measure(h)
+    prs.prs_destroy(h)
+    op = oracle.Params(shape)
+    ophi, ov = oracle.step(op, *oracle.init_random(op, 1), 5)
+    assert np.array_equal(phi, ophi)
+    od = oracle.measure(op, ophi, ov)
+    assert (nl, nw) == (od.n_links, od.n_wall)
+
+
+# ------------------------------------------------------------ diagnostics
+
+def _fields(shape):
+    yield "random", inp.random_field(shape, 31), 0.3 * inp.random_field(shape, 32)
+    W0 = 6.0
+    phi, v = inp.boosted_kink_pair(shape, W0, 0.4, axis=len(shape) - 1)
+    yield "boosted", phi, v
+    if shape[0] == shape[1]:
+        phi, v = inp.tilted_wall_pair(shape, W0)
+        yield "tilted", phi, v + 0.01
+    phi, v = inp.bubble(shape, min(shape) / 4, W0)
+    yield "bubble", phi, v - 0.02
+
+
+@pytest.mark.parametrize("precision", [prs.PRS_FP32, prs.PRS_FP64])
+@pytest.mark.parametrize("shape", [(64, 64), (37, 23), (24, 24, 24), (13, 11, 40)])
+def test_measure_parity(precision, shape):
+    for name, phi, v in _fields(shape):
+        np_dtype = np.float32 if precision == prs.PRS_FP32 else np.float64
+        phi = phi.astype(np_dtype)
+        v = v.astype(np_dtype)
+        sim = prs.Sim(shape, precision=precision, W0=6.0)
+        sim.set_state(phi, v, 0)
+        d = sim.measure()
+        sim.close()
+        od = oracle.measure(oracle.Params(shape, W0=6.0), phi.astype(np.float64), v.astype(np.float64))
+        assert (d["n_links"], d["n_wall"], d["n_vzero"], d["n_nonfinite"]) == \
+            (od.n_links, od.n_wall, od.n_vzero, od.n_nonfinite), name
+        tol = 1e-13 if precision == prs.PRS_FP64 else 1e-5
+        assert d["area_per_volume"] == pytest.approx(od.area_per_volume, rel=tol), name
+        assert d["gamma_v"] == pytest.approx(od.gamma_v, rel=tol), name
+
+
+def test_measure_nonfinite_and_empty():
+    shape = (16, 16)
+    sim = prs.Sim(shape, precision=prs.PRS_FP64)
+    phi = np.full((16, 16), 0.5)
+    v = np.zeros((16, 16))
+    sim.set_state(phi, v, 0)
+    d = sim.measure()
+    assert d["n_links"] == 0 and d["n_wall"] == 0 and d["gamma_v"] == 0.0 and d["area_per_volume"] == 0.0
+    phi[3, 4] = np.nan
+    sim.set_state(phi, v, 0)
+    out = prs.prs_diag()
+    rc = prs.load().prs_measure_ex(sim.handle, prs.ctypes.byref(out))
+    assert rc == prs.PRS_ENONFINITE and out.n_nonfinite == 1
+    sim.close()
+
+
+def test_measure_repeatable_bitwise():
+    """The FP64 reduction has a fixed order: repeated measurements agree bit for bit."""
+    shape = (96, 80, 40)
+    sim = prs.Sim(shape, precision=prs.PRS_FP32, seed=4)
+    sim.init()
+    sim.step(30)
+    a = sim.measure()
+    b = sim.measure()
+    sim.close()
+    assert a == b
+
+
+# ------------------------------------------------- full-size sampled checks
+
+def _subcube(field, centre, r):
+    """Periodic (2r+1)^D neighbourhood of ``centre`` (numpy index order) of a torch tensor, as FP64 numpy."""
+    import torch
+
+    idx = np.ix_(*[np.arange(c - r, c + r + 1) % n for c, n in zip(centre, field.shape)])
+    tidx = tuple(torch.as_tensor(i, device=field.device) for i in idx)
+    return field[tidx].cpu().numpy().astype(np.float64)
+
+
+def _sampled_step_check(shape, nsteps, tblock, nsamples=48, seed=0):
+    """Run nsteps on the full box, then check sampled sites against the oracle on periodic
+    (2 nsteps + 3)^D neighbourhoods (a site after k steps depends only on sites within k)."""
+    sim = prs.Sim(shape, precision=prs.PRS_FP32, seed=seed, tblock=tblock)
+    sim.init()
+    phi0_t, _, _ = sim.tensors()
+    fshape = tuple(phi0_t.shape)
+    rng = np.random.Generator(np.random.PCG64(77))
+    r = nsteps + 1
+    picks = [tuple(int(rng.integers(0, s)) for s in fshape) for _ in range(nsamples)]
+    picks += [tuple(0 for _ in fshape), tuple(s - 1 for s in fshape)]  # the periodic seams
+    subs = [_subcube(phi0_t, c, r) for c in picks]
+    sim.step(nsteps)
+    phi_t, v_t, n = sim.tensors()
+    assert n == nsteps
+    worst = 0.0
+    mid = tuple([r] * len(fshape))
+    for c, sub in zip(picks, subs):
+        p = oracle.Params(tuple(reversed(sub.shape)))
+        ophi, ov = oracle.step(p, sub, np.zeros_like(sub), nsteps)
+        worst = max(worst, abs(float(phi_t[c].item()) - ophi[mid]), abs(float(v_t[c].item()) - ov[mid]))
+    sim.close()
+    return worst
+
+
+def test_full_size_3d_1024_sampled():
+    """3D 1024^3 FP32, the benchmark's launch configuration: sampled sites after 4 steps."""
+    worst = _sampled_step_check((1024, 1024, 1024), 4, 0)
+    assert worst <= 1e-5  # |phi| < 1.1: absolute ~ relative
+
+
+def test_full_size_2d_4096_sampled():
+    worst = _sampled_step_check((4096, 4096), 6, 0)
+    assert worst <= 1e-5
