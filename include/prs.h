@@ -144,6 +144,24 @@ int prs_set_state(prs_sim* sim, const void* h_phi, const void* h_dphi, int64_t n
  * NULL).  The pointers stay valid until the next prs_step or prs_destroy. */
 int prs_device_state(prs_sim* sim, void** d_phi, void** d_dphi, int64_t* n);
 
+/* Wall diagnostics without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot let a library call cudaMalloc, e.g. an
+ * application that owns every device allocation through its own pool or budget,
+ * or a latency-critical loop where cudaMalloc's device-wide synchronisation is
+ * not acceptable.  It computes the same record as prs_measure_ex for the fields
+ * d_phi, d_dphi (caller-owned device memory, layout and precision of *params)
+ * using scratch held in a fixed array compiled into the library: 3 MiB of device
+ * memory on every GPU that loads it, kept until the process exits.  Limit:
+ * 2^30 sites (1024^3); larger lattices return PRS_EINVAL (see prs_last_error).
+ * The first call on a device looks up that array's address with the device
+ * current (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call shares the one array, which keeps the last call's
+ * contents (the call clears what must start at zero), so calls that overlap on
+ * the GPU, from several streams or threads, race: serialise them.  Synchronises
+ * `stream`.  out->step is -1 and out->eta 0: the fields carry no step index. */
+int prs_measure_noalloc(const prs_params* params, const void* d_phi, const void* d_dphi, void* stream,
+                        prs_diag* out);
+
 /* Release the run and the memory the library allocated for it (not bound buffers). */
 int prs_destroy(prs_sim* sim);
 

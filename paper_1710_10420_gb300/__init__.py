@@ -113,6 +113,7 @@ _SIGS = {
     "prs_destroy": (ctypes.c_int, [_VP]),
     "prs_coefficients": (ctypes.c_int, [_P, ctypes.c_int64, _DP]),
     "prs_default_tblock": (ctypes.c_int, [_P]),
+    "prs_measure_noalloc": (ctypes.c_int, [_P, _VP, _VP, _VP, ctypes.POINTER(prs_diag)]),
     "prs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "prs_last_error": (ctypes.c_char_p, []),
 }
@@ -226,6 +227,16 @@ def prs_device_state(sim):
 
 def prs_destroy(sim) -> None:
     _check(load().prs_destroy(sim), "prs_destroy")
+
+
+def prs_measure_noalloc(params: prs_params, d_phi, d_dphi, stream=None) -> prs_diag:
+    """Diagnostics of caller-owned device fields; the call allocates no device memory."""
+    d = prs_diag()
+    p = d_phi if isinstance(d_phi, int) else _ptr(d_phi)
+    v = d_dphi if isinstance(d_dphi, int) else _ptr(d_dphi)
+    _check(load().prs_measure_noalloc(ctypes.byref(params), p, v, stream, ctypes.byref(d)), "prs_measure_noalloc",
+           ok=(PRS_OK, PRS_ENONFINITE))
+    return d
 
 
 def prs_default_tblock(params: prs_params) -> int:

@@ -63,6 +63,10 @@ extern "C" const char* prs_strerror(int status)
 
 extern "C" const char* prs_last_error(void) { return g_last_error; }
 
+namespace prs {
+void record_error(const char* msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+}  // namespace prs
+
 // ------------------------------------------------------------- parameters
 
 static const double kPi = 3.14159265358979323846;

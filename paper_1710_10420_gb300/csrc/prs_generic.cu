@@ -310,3 +310,28 @@ cudaError_t launch_measure(const Geo& g, int precision, const void* phi, const v
 }
 
 }  // namespace prs
+
+namespace prs {
+
+// The same diagnostic kernel on a caller-chosen grid (one partial slot per block in scr).
+template <typename R>
+static cudaError_t measure_grid_t(const Geo& g, const void* phi, const void* dphi, const double rcd[6],
+                                  const DiagScratch& scr, int grid, cudaStream_t st)
+{
+    RunConst<R> rc = make_rc<R>(rcd);
+    if (g.dims == 3)
+        k_measure<R, 3><<<grid, 256, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
+    else
+        k_measure<R, 2><<<grid, 256, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_measure_on_grid(const Geo& g, int precision, const void* phi, const void* dphi,
+                                   const double rcd[6], const DiagScratch& scr, int grid, cudaStream_t st)
+{
+    if (grid < 1 || grid > scr.max_blocks) return cudaErrorInvalidValue;
+    if (precision == PRS_FP32) return measure_grid_t<float>(g, phi, dphi, rcd, scr, grid, st);
+    return measure_grid_t<double>(g, phi, dphi, rcd, scr, grid, st);
+}
+
+}  // namespace prs

@@ -67,4 +67,11 @@ int max_fused_steps(const Geo& g, int precision, bool repro);
 cudaError_t launch_measure(const Geo& g, int precision, const void* phi, const void* dphi, const double run_const[6],
                            const DiagScratch& scr, cudaStream_t st);
 
+// Store a message for prs_last_error() on this thread.
+void record_error(const char* msg);
+
+// The diagnostic kernel launched on exactly `grid` blocks (1 <= grid <= scr.max_blocks).
+cudaError_t launch_measure_on_grid(const Geo& g, int precision, const void* phi, const void* dphi,
+                                   const double run_const[6], const DiagScratch& scr, int grid, cudaStream_t st);
+
 }  // namespace prs
