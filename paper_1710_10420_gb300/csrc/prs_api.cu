@@ -28,7 +28,8 @@ struct prs_sim {
     int64_t n;           // step index of the state
     double rc[6];        // deta, 1/dx^2, 1/phi0^2, 2D, V0, phi0
     DiagScratch scr;
-    DiagAcc* h_result;   // pinned
+    DevStatus* d_status; // device: result, counter, error word
+    DevStatus* h_status; // pinned host copy
 };
 
 // ------------------------------------------------------------------ errors
@@ -164,16 +165,18 @@ extern "C" int prs_create(const prs_params* params, void* stream, prs_sim** out)
     s->rc[5] = params->phi0;
     s->scr.max_blocks = kMeasureBlocks;
     void* blob = nullptr;
-    size_t bytes = sizeof(DiagAcc) * (kMeasureBlocks + 1) + 256;
+    size_t bytes = sizeof(DiagAcc) * kMeasureBlocks + sizeof(DevStatus);
     if (cudaMalloc(&blob, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete s;
         return PRS_ENOMEM;
     }
     s->scr.partials = (DiagAcc*)blob;
-    s->scr.result = s->scr.partials + kMeasureBlocks;
-    s->scr.counter = (unsigned int*)((char*)blob + sizeof(DiagAcc) * (kMeasureBlocks + 1));
-    if (cudaMemset(blob, 0, bytes) != cudaSuccess || cudaMallocHost((void**)&s->h_result, sizeof(DiagAcc)) != cudaSuccess) {
+    s->d_status = (DevStatus*)(s->scr.partials + kMeasureBlocks);
+    s->scr.result = &s->d_status->result;
+    s->scr.counter = &s->d_status->counter;
+    if (cudaMemset(blob, 0, bytes) != cudaSuccess ||
+        cudaMallocHost((void**)&s->h_status, sizeof(DevStatus)) != cudaSuccess) {
         int r = cuda_fail(cudaGetLastError(), "prs_create");
         cudaFree(blob);
         delete s;
@@ -229,7 +232,7 @@ extern "C" int prs_destroy(prs_sim* s)
         cudaFree(s->dphi);
     }
     cudaFree(s->scr.partials);
-    cudaFreeHost(s->h_result);
+    cudaFreeHost(s->h_status);
     delete s;
     return PRS_OK;
 }
@@ -323,7 +326,8 @@ extern "C" int prs_step(prs_sim* s, int64_t nsteps)
         }
         const void* in = s->phi[s->cur];
         void* out = s->phi[1 - s->cur];
-        cudaError_t e = launch_step(s->g, s->p.precision, repro, in, out, s->dphi, c1, c2, cV, t, s->rc, s->stream);
+        cudaError_t e = launch_step(s->g, s->p.precision, repro, in, out, s->dphi, c1, c2, cV, t, s->rc,
+                                    &s->d_status->error, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
         s->cur = 1 - s->cur;
         done += t;
@@ -334,14 +338,28 @@ extern "C" int prs_step(prs_sim* s, int64_t nsteps)
 
 // ---------------------------------------------------------------- measure
 
+// After a synchronised read of h_status: a bounded device wait that gave up makes
+// the state untrustworthy; report it once and clear the word.
+static int check_device_error(prs_sim* s)
+{
+    if (s->h_status->error == 0) return PRS_OK;
+    snprintf(g_last_error, sizeof g_last_error, "device wait timed out (code %u)", s->h_status->error);
+    s->h_status->error = 0;
+    cudaMemsetAsync(&s->d_status->error, 0, sizeof(unsigned int), s->stream);
+    cudaStreamSynchronize(s->stream);
+    return PRS_ETIMEOUT;
+}
+
 static int measure_into(prs_sim* s, prs_diag* d)
 {
     if (!s->initialised) return PRS_ESTATE;
     cudaError_t e = launch_measure(s->g, s->p.precision, s->phi[s->cur], s->dphi, s->rc, s->scr, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "prs_measure launch");
-    PRS_CUDA(cudaMemcpyAsync(s->h_result, s->scr.result, sizeof(DiagAcc), cudaMemcpyDeviceToHost, s->stream));
+    PRS_CUDA(cudaMemcpyAsync(s->h_status, s->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->stream));
     PRS_CUDA(cudaStreamSynchronize(s->stream));
-    const DiagAcc& a = *s->h_result;
+    int err = check_device_error(s);
+    if (err) return err;
+    const DiagAcc& a = s->h_status->result;
     d->sum_w = a.sum_w;
     d->sum_ratio = a.sum_ratio;
     d->n_links = a.n_links;

@@ -51,6 +51,14 @@ struct DiagScratch {
     int max_blocks;
 };
 
+// Device words the host reads back with the diagnostics: the result, the
+// completion counter and the sticky error code of bounded waits (0 = none).
+struct DevStatus {
+    DiagAcc result;
+    unsigned int counter;
+    unsigned int error;
+};
+
 // Kernel launchers (prs_kernels.cu).  Each returns cudaSuccess or the launch error.
 cudaError_t launch_init_random(const Geo& g, int precision, uint64_t seed, void* phi, void* dphi, bool zero_dphi,
                                cudaStream_t st);
@@ -59,7 +67,7 @@ cudaError_t launch_init_random(const Geo& g, int precision, uint64_t seed, void*
 // dphi in place.  coef holds one entry per fused step (host memory, by value).
 cudaError_t launch_step(const Geo& g, int precision, bool repro, const void* phi_in, void* phi_out, void* dphi,
                         const double* c1, const double* c2, const double* cV, int nsteps_in_pass,
-                        const double run_const[6], cudaStream_t st);
+                        const double run_const[6], unsigned int* err, cudaStream_t st);
 
 // Largest number of steps one launch_step pass can fuse for this geometry/precision.
 int max_fused_steps(const Geo& g, int precision, bool repro);

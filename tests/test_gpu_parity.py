@@ -110,7 +110,11 @@ def test_fp64_fma_close(shape):
     assert _rel(v, ov) <= 1e-12
 
 
-FP32_CASES = [(128, 128), (256, 64), (130, 66), (17, 19), (64, 64, 64), (32, 16, 24), (20, 12, 9), (128, 8, 8)]
+# generic kernel: x side not a multiple of 128 (or too few rows for a tile)
+# fast kernel: x side a multiple of 128; 3D tiles of 4096/nx rows, 2D bands of 4096/nx rows
+FP32_CASES = [(130, 66), (17, 19), (64, 64, 64), (32, 16, 24), (20, 12, 9), (128, 8, 8),
+              (128, 128), (256, 64), (4096, 6), (2048, 40), (1024, 12),
+              (128, 64, 40), (256, 32, 20), (512, 16, 24), (1024, 8, 10), (128, 32, 3), (256, 16, 17)]
 
 
 @pytest.mark.parametrize("shape", FP32_CASES)
