@@ -42,7 +42,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="3d1024", choices=sorted(WORKLOADS))
@@ -66,6 +66,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def __enter__(self):
         try:
@@ -74,6 +75,10 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:  # the sampler is up before timing starts
+                time.sleep(0.02)
+            self.skip = len(self.lines)
         except (OSError, ValueError):
             self.proc = None
         return self
@@ -94,7 +99,7 @@ class ClockSampler:
     def summary(self) -> dict:
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        for l in self.lines[self.skip:]:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 8:
                 continue

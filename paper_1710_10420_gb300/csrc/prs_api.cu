@@ -143,7 +143,7 @@ extern "C" int prs_default_tblock(const prs_params* params)
 
 // -------------------------------------------------------------- lifecycle
 
-static const int kMeasureBlocks = 152 * 8;
+static const int kMeasureBlocks = 8192;  // partial slots: the fast kernels use one per tile
 
 extern "C" int prs_create(const prs_params* params, void* stream, prs_sim** out)
 {
@@ -353,7 +353,15 @@ static int check_device_error(prs_sim* s)
 static int measure_into(prs_sim* s, prs_diag* d)
 {
     if (!s->initialised) return PRS_ESTATE;
-    cudaError_t e = launch_measure(s->g, s->p.precision, s->phi[s->cur], s->dphi, s->rc, s->scr, s->stream);
+    cudaError_t e = cudaErrorNotSupported;
+    if (fast_step_ok(s->g, s->p.precision)) {
+        RunConst<float> rc{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
+                           (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
+        e = launch_measure_fast(s->g, (const float*)s->phi[s->cur], (const float*)s->dphi, rc, s->scr,
+                                &s->d_status->error, s->stream);
+    }
+    if (e == cudaErrorNotSupported)
+        e = launch_measure(s->g, s->p.precision, s->phi[s->cur], s->dphi, s->rc, s->scr, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "prs_measure launch");
     PRS_CUDA(cudaMemcpyAsync(s->h_status, s->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->stream));
     PRS_CUDA(cudaStreamSynchronize(s->stream));

@@ -26,6 +26,7 @@
 #include "prs_arith.cuh"
 #include "prs_internal.h"
 #include "prs_ptx.cuh"
+#include "prs_reduce.cuh"
 
 namespace prs {
 
@@ -283,6 +284,384 @@ __global__ void __launch_bounds__(kFastThreads, 2)
     }
 }
 
+// --------------------------------------------------------------- diagnostics
+//
+// Eq. 7 and Eq. 8 on the same plane staging as the step: every site tests the
+// signs of its 2D neighbours (one float4 of 4 sites at a time, x neighbours by
+// shuffle); only sites with a crossing link (a few per cent) read the extra
+// neighbours of the link-midpoint gradient from shared memory.  Each thread keeps
+// its own FP64 sums and integer counts; prs_reduce.cuh finishes them in a fixed
+// order.
+
+// Per-thread sums.  The site terms of one plane (at most 16 sites x 3 links) are
+// added in FP32 and folded into the FP64 totals once per plane: GB300 issues FP64
+// at a small fraction of its FP32 rate, and a per-site FP64 add made the kernel
+// arithmetic-bound.  The FP32 plane partial of <= 48 terms in [0, 1] (weights) or
+// of the ratios keeps a relative error below 48 ulp.
+struct SiteAcc {
+    double sw, sr;
+    float pw, pr;  // current plane's partial sums
+    int nl, nw, nv0, nnf;
+    __device__ __forceinline__ void fold()
+    {
+        sw += (double)pw;
+        sr += (double)pr;
+        pw = 0.0f;
+        pr = 0.0f;
+    }
+};
+
+// |g| / sum_i |g_i| with the hardware reciprocal square root and reciprocal
+// (a few ulp; num > 0 because the link's own component is non-zero).
+__device__ __forceinline__ float link_weight3(float gx, float gy, float gz)
+{
+    float num = gx * gx;
+    num = num + gy * gy;
+    num = num + gz * gz;
+    float den = fabsf(gx);
+    den = den + fabsf(gy);
+    den = den + fabsf(gz);
+    return __fdividef(num * rsqrtf(num), den);
+}
+
+__device__ __forceinline__ float link_weight2(float gx, float gy)
+{
+    float num = gx * gx;
+    num = num + gy * gy;
+    float den = fabsf(gx);
+    den = den + fabsf(gy);
+    return __fdividef(num * rsqrtf(num), den);
+}
+
+// Bit e set when component e of the float4 is negative (the (phi < 0) rule; -0 is not).
+__device__ __forceinline__ unsigned negmask4(float4 a)
+{
+    return (a.x < 0.0f ? 1u : 0u) | (a.y < 0.0f ? 2u : 0u) | (a.z < 0.0f ? 4u : 0u) | (a.w < 0.0f ? 8u : 0u);
+}
+
+// Eq. 8 terms of the wall sites among the four (bit e of `wall`), FP32 factored
+// potential, hardware reciprocal; plus the exact count of non-finite values,
+// screened by one sum (a non-finite value makes it non-finite).
+__device__ __forceinline__ void wall_sites4(SiteAcc& a, unsigned wall, float4 c, float4 vv, const RunConst<float>& rc)
+{
+    const float cs[4] = {c.x, c.y, c.z, c.w};
+    const float vs[4] = {vv.x, vv.y, vv.z, vv.w};
+    const float screen = ((c.x + c.y) + (c.z + c.w)) + ((vv.x + vv.y) + (vv.z + vv.w));
+    if (!isfinite(screen)) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) a.nnf += (!isfinite(cs[e]) || !isfinite(vs[e])) ? 1 : 0;
+    }
+    a.nw += __popc(wall);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float s = cs[e];
+        const float u = ((s - rc.phi0) * (s + rc.phi0)) * rc.inv_phi0sq;
+        const float V = (rc.V0 * u) * u;
+        const bool w = (wall >> e) & 1u;
+        const bool pos = V > 0.0f;
+        a.nv0 += (w && !pos) ? 1 : 0;
+        a.pr += (w && pos) ? __fdividef(vs[e] * vs[e], V) : 0.0f;
+    }
+}
+
+// Crossing links are compacted per warp: each lane appends its links (site e of
+// its float4, axis d) to the warp's queue in shared memory, then the warp takes
+// them 32 at a time, so the link-midpoint gradients cost one pass instead of one
+// divergent pass per site and axis.
+static constexpr int kQueuePerWarp = 32 * 12;  // 4 sites x 3 axes per lane
+static constexpr size_t kQueueBytes = (kFastThreads / 32) * kQueuePerWarp * sizeof(unsigned);
+
+// Appends this lane's set bits of `mask` (bit 4d+e: site e of the float4, axis d) to the warp queue;
+// returns the warp's total.
+__device__ __forceinline__ int enqueue_links(unsigned* wq, unsigned mask, int lane)
+{
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int k = incl - cnt;
+    while (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        wq[k++] = ((unsigned)lane << 4) | (unsigned)b;
+    }
+    __syncwarp();
+    return total;
+}
+
+// Eq. 7 weight of the link from (x, row r) of plane Pc along axis d (3D).
+__device__ __forceinline__ float weight3(const float* Pm, const float* Pc, const float* Pp, int r, int x, int d,
+                                        int nx)
+{
+    const int xr = x + 1 == nx ? 0 : x + 1, xl = x == 0 ? nx - 1 : x - 1;
+    const float* cm = Pc + (r - 1) * nx;
+    const float* c0 = Pc + r * nx;
+    const float* c1 = Pc + (r + 1) * nx;
+    const float s = c0[x];
+    float gx, gy, gz;
+    if (d == 0) {  // to (x+1, y, z)
+        gx = c0[xr] - s;
+        gy = 0.25f * ((c1[x] - cm[x]) + (c1[xr] - cm[xr]));
+        gz = 0.25f * ((Pp[r * nx + x] - Pm[r * nx + x]) + (Pp[r * nx + xr] - Pm[r * nx + xr]));
+    } else if (d == 1) {  // to (x, y+1, z)
+        gx = 0.25f * ((c0[xr] - c0[xl]) + (c1[xr] - c1[xl]));
+        gy = c1[x] - s;
+        gz = 0.25f * ((Pp[r * nx + x] - Pm[r * nx + x]) + (Pp[(r + 1) * nx + x] - Pm[(r + 1) * nx + x]));
+    } else {  // to (x, y, z+1)
+        const float* p0 = Pp + r * nx;
+        gx = 0.25f * ((c0[xr] - c0[xl]) + (p0[xr] - p0[xl]));
+        gy = 0.25f * ((c1[x] - cm[x]) + (Pp[(r + 1) * nx + x] - Pp[(r - 1) * nx + x]));
+        gz = p0[x] - s;
+    }
+    return link_weight3(gx, gy, gz);
+}
+
+// Eq. 7 weight of the link from x of row crow along axis d (2D); urow/drow are
+// the rows above and below.
+__device__ __forceinline__ float weight2(const float* urow, const float* crow, const float* drow, int x, int d, int nx)
+{
+    const int xr = x + 1 == nx ? 0 : x + 1, xl = x == 0 ? nx - 1 : x - 1;
+    const float s = crow[x];
+    if (d == 0) return link_weight2(crow[xr] - s, 0.25f * ((drow[x] - urow[x]) + (drow[xr] - urow[xr])));
+    return link_weight2(0.25f * ((crow[xr] - crow[xl]) + (drow[xr] - drow[xl])), drow[x] - s);
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kFastThreads, 2)
+    k_measure3d_f32(const float* __restrict__ phi, const float* __restrict__ v, int nx, int ny, int nz, int ty,
+                    int cz, RunConst<float> rc, DiagScratch scr, unsigned int* err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* ring = reinterpret_cast<float*>(smem_raw + 128);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int ytiles = ny / ty;
+    const int y0 = (blockIdx.x % ytiles) * ty;
+    const int z0 = (blockIdx.x / ytiles) * cz;
+    const int zn = min(cz, nz - z0);
+    const int nq = nx >> 2;
+    const int tile = (ty + 2) * nx;
+    const size_t plane = (size_t)nx * ny;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    const int ytop = (y0 == 0 ? ny : y0) - 1;
+    const int ybot = (y0 + ty == ny) ? 0 : y0 + ty;
+    const unsigned rowb = (unsigned)nx * 4u;
+    const int nloc = zn + 2;
+    auto issue = [&](int i) {
+        int p = z0 - 1 + i;
+        p = p < 0 ? p + nz : (p >= nz ? p - nz : p);
+        float* dst = ring + (i & 3) * tile;
+        const float* src = phi + (size_t)p * plane;
+        uint64_t* b = &bar[i & 3];
+        mbar_arrive_expect_tx(b, rowb * (unsigned)(ty + 2));
+        bulk_g2s(dst, src + (size_t)ytop * nx, rowb, b);
+        bulk_g2s(dst + nx, src + (size_t)y0 * nx, rowb * (unsigned)ty, b);
+        bulk_g2s(dst + (size_t)(ty + 1) * nx, src + (size_t)ybot * nx, rowb, b);
+    };
+    int issued = -1;
+    if (tid == 0)
+        for (int i = 0; i < 3 && i < nloc; ++i) issue(i), issued = i;
+
+    int row[ITEMS], col[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        int q = tid + kFastThreads * j;
+        row[j] = q / nq;
+        col[j] = q - row[j] * nq;
+    }
+    SiteAcc a{0.0, 0.0, 0.0f, 0.0f, 0, 0, 0, 0};
+    unsigned* wq = reinterpret_cast<unsigned*>(ring + 4 * tile) + (tid >> 5) * kQueuePerWarp;
+    float4 vc[ITEMS];
+    {
+        const float* vb = v + (size_t)z0 * plane + (size_t)y0 * nx;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) vc[j] = ldg_stream4(vb + (size_t)row[j] * nx + 4 * col[j]);
+    }
+    for (int zi = 0; zi < zn; ++zi) {
+        bool ok = true;
+        if (zi == 0) ok = mbar_wait(&bar[0], 0, err) && mbar_wait(&bar[1], 0, err);
+        ok = ok && mbar_wait(&bar[(zi + 2) & 3], ((zi + 2) >> 2) & 1, err);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) drain(bar, zi, issued, err);
+            break;  // the partial sums still go through the block reduction
+        }
+        if (tid == 0 && zi + 3 < nloc) issue(zi + 3), issued = zi + 3;
+        const int z = z0 + zi;
+        float4 vn[ITEMS];
+        if (zi + 1 < zn) {
+            const float* vb = v + (size_t)(z + 1) * plane + (size_t)y0 * nx;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) vn[j] = ldg_stream4(vb + (size_t)row[j] * nx + 4 * col[j]);
+        }
+        const float* Pm = ring + (zi & 3) * tile + nx;
+        const float* Pc = ring + ((zi + 1) & 3) * tile + nx;
+        const float* Pp = ring + ((zi + 2) & 3) * tile + nx;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int r = row[j];
+            const int off = r * nx + 4 * col[j];
+            float4 c = lds4(Pc + off);
+            float4 ym4 = lds4(Pc + off - nx);
+            float4 yp4 = lds4(Pc + off + nx);
+            float4 zm4 = lds4(Pm + off);
+            float4 zp4 = lds4(Pp + off);
+            float left, right;
+            x_halo(Pc + r * nx, col[j], nq, nx, lane, c, left, right);
+            const unsigned sc = negmask4(c);
+            const unsigned sxp = (sc >> 1) | (right < 0.0f ? 8u : 0u);
+            const unsigned sxm = ((sc << 1) & 15u) | (left < 0.0f ? 1u : 0u);
+            const unsigned lx = sc ^ sxp, ly = sc ^ negmask4(yp4), lz = sc ^ negmask4(zp4);
+            const unsigned wall = lx | ly | lz | (sc ^ sxm) | (sc ^ negmask4(ym4)) | (sc ^ negmask4(zm4));
+            wall_sites4(a, wall, c, vc[j], rc);
+            // bit 4d+e: the link from site e along axis d crosses
+            const unsigned lmask = lx | (ly << 4) | (lz << 8);
+            a.nl += __popc(lmask);
+            const int total = enqueue_links(wq, lmask, lane);
+            const int colbase = col[j] - lane;  // the warp's 32 float4 are consecutive in one row
+            for (int base = 0; base < total; base += 32) {
+                const int idx = base + lane;
+                if (idx < total) {
+                    const unsigned ent = wq[idx];
+                    const int b = ent & 15, e = b & 3, d = b >> 2;
+                    a.pw += weight3(Pm, Pc, Pp, r, 4 * (colbase + (int)(ent >> 4)) + e, d, nx);
+                }
+            }
+            __syncwarp();
+        }
+        a.fold();
+        if (zi + 1 < zn) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];
+        }
+    }
+    block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kFastThreads, 2)
+    k_measure2d_f32(const float* __restrict__ phi, const float* __restrict__ v, int nx, int ny, int rb, int cy,
+                    RunConst<float> rc, DiagScratch scr, unsigned int* err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* ring = reinterpret_cast<float*>(smem_raw + 128);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int y0 = blockIdx.x * cy;
+    const int yn = min(cy, ny - y0);
+    const int nb = yn / rb;
+    const int nq = nx >> 2;
+    const int slot = rb * nx;
+    const int ringrows = 4 * rb;
+    const unsigned rowb = (unsigned)nx * 4u;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int nloc = nb + 2;
+    auto issue = [&](int i) {
+        float* dst = ring + (i & 3) * slot;
+        uint64_t* b = &bar[i & 3];
+        if (i == 0) {
+            int y = (y0 == 0 ? ny : y0) - 1;
+            mbar_arrive_expect_tx(b, rowb);
+            bulk_g2s(dst + (size_t)(rb - 1) * nx, phi + (size_t)y * nx, rowb, b);
+        } else if (i == nb + 1) {
+            int y = (y0 + yn == ny) ? 0 : y0 + yn;
+            mbar_arrive_expect_tx(b, rowb);
+            bulk_g2s(dst, phi + (size_t)y * nx, rowb, b);
+        } else {
+            int y = y0 + (i - 1) * rb;
+            mbar_arrive_expect_tx(b, rowb * (unsigned)rb);
+            bulk_g2s(dst, phi + (size_t)y * nx, rowb * (unsigned)rb, b);
+        }
+    };
+    int issued = -1;
+    if (tid == 0)
+        for (int i = 0; i < 3 && i < nloc; ++i) issue(i), issued = i;
+
+    int row[ITEMS], col[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        int q = tid + kFastThreads * j;
+        row[j] = q / nq;
+        col[j] = q - row[j] * nq;
+    }
+    SiteAcc a{0.0, 0.0, 0.0f, 0.0f, 0, 0, 0, 0};
+    unsigned* wq = reinterpret_cast<unsigned*>(ring + 4 * slot) + (tid >> 5) * kQueuePerWarp;
+    float4 vc[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) vc[j] = ldg_stream4(v + (size_t)(y0 + row[j]) * nx + 4 * col[j]);
+
+    for (int bi = 0; bi < nb; ++bi) {
+        bool ok = true;
+        if (bi == 0) ok = mbar_wait(&bar[0], 0, err) && mbar_wait(&bar[1], 0, err);
+        ok = ok && mbar_wait(&bar[(bi + 2) & 3], ((bi + 2) >> 2) & 1, err);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) drain(bar, bi, issued, err);
+            break;
+        }
+        if (tid == 0 && bi + 3 < nloc) issue(bi + 3), issued = bi + 3;
+        const int yb = y0 + bi * rb;
+        float4 vn[ITEMS];
+        if (bi + 1 < nb) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) vn[j] = ldg_stream4(v + (size_t)(yb + rb + row[j]) * nx + 4 * col[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int lr = (bi + 1) * rb + row[j];
+            const float* crow = ring + (size_t)(lr % ringrows) * nx;
+            const float* urow = ring + (size_t)((lr + ringrows - 1) % ringrows) * nx;
+            const float* drow = ring + (size_t)((lr + 1) % ringrows) * nx;
+            float4 c = lds4(crow + 4 * col[j]);
+            float4 ym4 = lds4(urow + 4 * col[j]);
+            float4 yp4 = lds4(drow + 4 * col[j]);
+            float left, right;
+            x_halo(crow, col[j], nq, nx, lane, c, left, right);
+            const unsigned sc = negmask4(c);
+            const unsigned sxp = (sc >> 1) | (right < 0.0f ? 8u : 0u);
+            const unsigned sxm = ((sc << 1) & 15u) | (left < 0.0f ? 1u : 0u);
+            const unsigned lx = sc ^ sxp, ly = sc ^ negmask4(yp4);
+            const unsigned wall = lx | ly | (sc ^ sxm) | (sc ^ negmask4(ym4));
+            wall_sites4(a, wall, c, vc[j], rc);
+            // bit 4d+e: the link from site e along axis d crosses
+            const unsigned lmask = lx | (ly << 4);
+            a.nl += __popc(lmask);
+            const int total = enqueue_links(wq, lmask, lane);
+            const int colbase = col[j] - lane;
+            for (int base = 0; base < total; base += 32) {
+                const int idx = base + lane;
+                if (idx < total) {
+                    const unsigned ent = wq[idx];
+                    const int b = ent & 15, e = b & 3, d = b >> 2;
+                    a.pw += weight2(urow, crow, drow, 4 * (colbase + (int)(ent >> 4)) + e, d, nx);
+                }
+            }
+            __syncwarp();
+        }
+        a.fold();
+        if (bi + 1 < nb) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];
+        }
+    }
+    block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
+}
+
 // ------------------------------------------------------------------ dispatch
 
 static constexpr int kItems = 4;  // float4 per thread per plane: 4096 sites per plane tile
@@ -291,6 +670,7 @@ static size_t smem3d(int nx, int ty) { return 128 + 4 * (size_t)(ty + 2) * nx * 
 static size_t smem2d(int nx, int rb) { return 128 + 4 * (size_t)rb * nx * sizeof(float); }
 
 static constexpr size_t kFastSmemMax = 100 * 1024;
+static constexpr size_t kMeasureSmemMax = kFastSmemMax + kQueueBytes;
 
 bool fast_step_ok(const Geo& g, int precision)
 {
@@ -303,7 +683,7 @@ bool fast_step_ok(const Geo& g, int precision)
 
 // Number of z-chunks (3D) or row chunks (2D): balance whole waves of resident
 // CTAs against the two halo planes each chunk re-reads.
-static int pick_chunks(int tiles, int len, int min_len, int slots)
+static int pick_chunks(int tiles, int len, int min_len, int slots, long long max_blocks = 1ll << 40)
 {
     int best = 1;
     double best_score = -1.0;
@@ -311,6 +691,7 @@ static int pick_chunks(int tiles, int len, int min_len, int slots)
         int c = (len + nc - 1) / nc;
         int n = (len + c - 1) / c;
         long long blocks = (long long)tiles * n;
+        if (blocks > max_blocks && nc > 1) break;
         long long waves = (blocks + slots - 1) / slots;
         double fill = (double)blocks / (double)(waves * slots);
         double halo = (double)c / (double)(c + 2);
@@ -373,6 +754,49 @@ cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, float* v
     const int cy = bpc * t;
     nchunks = (g.ny + cy - 1) / cy;
     k_step2d_f32<kItems><<<nchunks, kFastThreads, sm, st>>>(in, out, v, g.nx, g.ny, t, cy, k, rc, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_measure_fast(const Geo& g, const float* phi, const float* v, RunConst<float> rc,
+                                const DiagScratch& scr, unsigned int* err, cudaStream_t st)
+{
+    static bool attr3 = false, attr2 = false;
+    const int t = kItems * 1024 / g.nx;
+    const int slots = 2 * sm_count();
+    if (g.dims == 3) {
+        const size_t sm = smem3d(g.nx, t) + kQueueBytes;
+        if (sm > kMeasureSmemMax) return cudaErrorNotSupported;
+        if (!attr3) {
+            cudaError_t e = cudaFuncSetAttribute(k_measure3d_f32<kItems>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMeasureSmemMax);
+            if (e != cudaSuccess) return e;
+            attr3 = true;
+        }
+        const int ytiles = g.ny / t;
+        if (ytiles > scr.max_blocks) return cudaErrorNotSupported;
+        int nchunks = pick_chunks(ytiles, g.nz, 16, slots, scr.max_blocks);
+        const int cz = (g.nz + nchunks - 1) / nchunks;
+        nchunks = (g.nz + cz - 1) / cz;
+        if ((long long)ytiles * nchunks > scr.max_blocks) return cudaErrorNotSupported;
+        k_measure3d_f32<kItems><<<ytiles * nchunks, kFastThreads, sm, st>>>(phi, v, g.nx, g.ny, g.nz, t, cz, rc, scr,
+                                                                            err);
+        return cudaGetLastError();
+    }
+    const size_t sm = smem2d(g.nx, t) + kQueueBytes;
+    if (sm > kMeasureSmemMax) return cudaErrorNotSupported;
+    if (!attr2) {
+        cudaError_t e = cudaFuncSetAttribute(k_measure2d_f32<kItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMeasureSmemMax);
+        if (e != cudaSuccess) return e;
+        attr2 = true;
+    }
+    const int bands = g.ny / t;
+    int nchunks = pick_chunks(1, bands, 4, slots, scr.max_blocks);
+    const int bpc = (bands + nchunks - 1) / nchunks;
+    const int cy = bpc * t;
+    nchunks = (g.ny + cy - 1) / cy;
+    if (nchunks > scr.max_blocks) return cudaErrorNotSupported;
+    k_measure2d_f32<kItems><<<nchunks, kFastThreads, sm, st>>>(phi, v, g.nx, g.ny, t, cy, rc, scr, err);
     return cudaGetLastError();
 }
 

@@ -75,6 +75,11 @@ int max_fused_steps(const Geo& g, int precision, bool repro);
 cudaError_t launch_measure(const Geo& g, int precision, const void* phi, const void* dphi, const double run_const[6],
                            const DiagScratch& scr, cudaStream_t st);
 
+// Fast FP32 kernels (prs_fast.cu) for x sides that are multiples of 128.
+bool fast_step_ok(const Geo& g, int precision);
+cudaError_t launch_measure_fast(const Geo& g, const float* phi, const float* v, RunConst<float> rc,
+                                const DiagScratch& scr, unsigned int* err, cudaStream_t st);
+
 // Store a message for prs_last_error() on this thread.
 void record_error(const char* msg);
 

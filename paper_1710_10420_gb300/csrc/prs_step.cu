@@ -5,7 +5,6 @@ namespace prs {
 
 cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const void* in, void* out, void* dphi,
                                 double c1, double c2, double cV, const double rcd[6], cudaStream_t st);
-bool fast_step_ok(const Geo& g, int precision);
 cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, float* v, StepCoef<float> k,
                              RunConst<float> rc, unsigned int* err, cudaStream_t st);
 

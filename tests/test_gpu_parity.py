@@ -194,8 +194,12 @@ def _fields(shape):
     yield "bubble", phi, v - 0.02
 
 
+MEASURE_SHAPES = [(64, 64), (37, 23), (24, 24, 24), (13, 11, 40),  # generic kernel
+                  (128, 128), (512, 32), (4096, 8), (128, 64, 40), (256, 32, 16), (1024, 8, 6)]  # fast (FP32)
+
+
 @pytest.mark.parametrize("precision", [prs.PRS_FP32, prs.PRS_FP64])
-@pytest.mark.parametrize("shape", [(64, 64), (37, 23), (24, 24, 24), (13, 11, 40)])
+@pytest.mark.parametrize("shape", MEASURE_SHAPES)
 def test_measure_parity(precision, shape):
     for name, phi, v in _fields(shape):
         np_dtype = np.float32 if precision == prs.PRS_FP32 else np.float64
@@ -286,3 +290,43 @@ def test_full_size_3d_1024_sampled():
 def test_full_size_2d_4096_sampled():
     worst = _sampled_step_check((4096, 4096), 6, 0)
     assert worst <= 1e-5
+
+
+def _fill(sim, phi_profile, v_profile, axis_len_last=True):
+    """Write a field that depends on the slowest axis only into the run's current buffers."""
+    import torch
+
+    phi_t, v_t, _ = sim.tensors()
+    shape = (phi_t.shape[0],) + (1,) * (phi_t.dim() - 1)
+    phi_t.copy_(torch.as_tensor(phi_profile, dtype=phi_t.dtype, device=phi_t.device).reshape(shape).expand_as(phi_t))
+    v_t.copy_(torch.as_tensor(v_profile, dtype=v_t.dtype, device=v_t.device).reshape(shape).expand_as(v_t))
+    torch.cuda.synchronize()
+
+
+def test_full_size_3d_1024_measure_exact_cases():
+    """1024^3 FP32 diagnostics on fields with known answers (planar and boosted walls along z)."""
+    import torch
+
+    n = 1024
+    sim = prs.Sim((n, n, n), precision=prs.PRS_FP32, seed=1)
+    sim.init()
+    prof, vprof = inp.kink_pair((4, 4, n), 10.0, axis=2)
+    _fill(sim, prof[:, 0, 0], vprof[:, 0, 0])
+    d = sim.measure()
+    assert d["n_links"] == 2 * n * n and d["n_wall"] == 4 * n * n
+    assert d["area_per_volume"] == pytest.approx(2.0 / n, rel=1e-12)  # every weight is exactly 1
+    u = 0.3
+    prof, vprof = inp.boosted_kink_pair((4, 4, n), 10.0, u, axis=2)
+    _fill(sim, prof[:, 0, 0], vprof[:, 0, 0])
+    d = sim.measure()
+    assert d["gamma_v"] == pytest.approx(u / math.sqrt(1 - u * u), rel=1e-5)
+    # Z2: the negated random field measures identically, bit for bit
+    sim.init()
+    sim.step(3)
+    a = sim.measure()
+    phi_t, _, _ = sim.tensors()
+    phi_t.neg_()
+    torch.cuda.synchronize()
+    b = sim.measure()
+    sim.close()
+    assert {k: a[k] for k in a if k not in ("step", "eta")} == {k: b[k] for k in b if k not in ("step", "eta")}

@@ -4,9 +4,12 @@ Such callers (an application that owns every device allocation, or a loop that
 cannot afford cudaMalloc's device-wide synchronisation) get the same record as
 prs_measure_ex, computed with scratch in a fixed array compiled into the library.
 These tests call it through the C ABI on fields held by an ordinary run and
-compare it with prs_measure_ex: counts exactly, A/V and gamma v to 1e-13 relative
-(the two differ only in the order of the FP64 reduction).  The file is collected
-last so that a failure here comes after every other test has run.
+compare it with prs_measure_ex: counts exactly; A/V and gamma v to 1e-13 relative
+in FP64 (only the order of the FP64 reduction differs) and to the FP32 diagnostic
+tolerance of the parity tests, 1e-5, in FP32 (for x sides that are multiples of
+128, prs_measure_ex uses the plane-staged kernel, whose per-site float rounding
+may differ).  The file is collected last so that a failure here comes after
+every other test has run.
 """
 import ctypes
 
@@ -26,10 +29,11 @@ def _lib():
     prs.load(build=True)
 
 
-def _check_same(d, ref):
+def _check_same(d, ref, precision):
+    tol = 1e-13 if precision == prs.PRS_FP64 else 1e-5
     assert (d.n_links, d.n_wall, d.n_vzero, d.n_nonfinite) == (ref.n_links, ref.n_wall, ref.n_vzero, ref.n_nonfinite)
-    assert d.area_per_volume == pytest.approx(ref.area_per_volume, rel=1e-13)
-    assert d.gamma_v == pytest.approx(ref.gamma_v, rel=1e-13)
+    assert d.area_per_volume == pytest.approx(ref.area_per_volume, rel=tol)
+    assert d.gamma_v == pytest.approx(ref.gamma_v, rel=tol)
 
 
 def _sim(shape, precision, seed, nsteps):
@@ -48,7 +52,7 @@ def test_noalloc_matches_measure_twice(precision, shape):
     stream = sim.stream.cuda_stream
     for _ in range(2):
         d = prs.prs_measure_noalloc(sim.params, d_phi, d_dphi, stream)
-        _check_same(d, ref)
+        _check_same(d, ref, precision)
     sim.close()
 
 
@@ -57,9 +61,9 @@ def test_noalloc_alternating_runs():
     a = _sim((128, 96), prs.PRS_FP32, seed=1, nsteps=10)
     b = _sim((40, 36, 30), prs.PRS_FP64, seed=2, nsteps=10)
     ra, rb = prs.prs_measure_ex(a.handle), prs.prs_measure_ex(b.handle)
-    for sim, ref in [(a, ra), (b, rb), (a, ra)]:
+    for sim, ref, prec in [(a, ra, prs.PRS_FP32), (b, rb, prs.PRS_FP64), (a, ra, prs.PRS_FP32)]:
         p, v, _ = prs.prs_device_state(sim.handle)
-        _check_same(prs.prs_measure_noalloc(sim.params, p, v, sim.stream.cuda_stream), ref)
+        _check_same(prs.prs_measure_noalloc(sim.params, p, v, sim.stream.cuda_stream), ref, prec)
     a.close()
     b.close()
 
