@@ -165,6 +165,28 @@ int prs_measure_noalloc(const prs_params* params, const void* d_phi, const void*
 /* Release the run and the memory the library allocated for it (not bound buffers). */
 int prs_destroy(prs_sim* sim);
 
+/* ---------------------------------------------------------------- adjoint
+ * Not in the paper: gradients of a smooth stand-in for the wall diagnostics
+ * (PRS_OBS_GRAD_ENERGY or PRS_OBS_SMOOTH_AREA with smoothing width eps_smooth),
+ * by the hand-written transpose of the leapfrog step of Eqs. 3-6. */
+
+/* J of the current field (FP64 reduction); synchronises. */
+int prs_observable(prs_sim* sim, int observable, double eps_smooth, double* J);
+
+/* Advance the run by nsteps (like prs_step) and return J of the final field with
+ * its gradient with respect to the state at the start of the call and to alpha:
+ *   *J, *dJ_dalpha (host, FP64);
+ *   d_dJ_dphi_init, d_dJ_dv_init: caller-owned device arrays of the run's layout and
+ *   precision (either may be NULL), receiving dJ/dphi and dJ/d(dphi) at the start.
+ * Memory: a checkpoint of (phi, dphi) every ckpt_every steps plus ckpt_every-1
+ * states of one segment, allocated for the call and freed before it returns.
+ * Reverse sweep per segment: recompute its states from the checkpoint, then apply
+ *   lt = lv' + deta lphi',  lphi = lphi' + c2 (L lt - f'(phi) lt),  lv = c1 lt,
+ *   dJ/dalpha += sum lt (dc1/dalpha dphi + dc2/dalpha (L phi - f(phi))).
+ * On return the run holds the state at step n+nsteps.  Synchronises. */
+int prs_adjoint(prs_sim* sim, int64_t nsteps, int observable, double eps_smooth, int64_t ckpt_every, double* J,
+                double* dJ_dalpha, void* d_dJ_dphi_init, void* d_dJ_dv_init);
+
 /* Step-n coefficients as the library computes them on the host in FP64:
  * out[0] = c1 = (1-delta_n)/(1+delta_n), out[1] = c2 = deta/(1+delta_n) (Eq. 4, 6),
  * out[2] = cV = 4 V0 a_n^beta / phi0^2 (force prefactor), out[3] = delta_n,

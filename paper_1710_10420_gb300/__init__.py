@@ -113,6 +113,9 @@ _SIGS = {
     "prs_destroy": (ctypes.c_int, [_VP]),
     "prs_coefficients": (ctypes.c_int, [_P, ctypes.c_int64, _DP]),
     "prs_default_tblock": (ctypes.c_int, [_P]),
+    "prs_observable": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, _DP]),
+    "prs_adjoint": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _DP, _DP, _VP,
+                                   _VP]),
     "prs_measure_noalloc": (ctypes.c_int, [_P, _VP, _VP, _VP, ctypes.POINTER(prs_diag)]),
     "prs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "prs_last_error": (ctypes.c_char_p, []),
@@ -239,6 +242,21 @@ def prs_measure_noalloc(params: prs_params, d_phi, d_dphi, stream=None) -> prs_d
     return d
 
 
+def prs_observable(sim, observable: int, eps_smooth: float = 0.1) -> float:
+    J = ctypes.c_double()
+    _check(load().prs_observable(sim, observable, eps_smooth, ctypes.byref(J)), "prs_observable")
+    return J.value
+
+
+def prs_adjoint(sim, nsteps: int, observable: int, eps_smooth: float = 0.1, ckpt_every: int = 64, d_dJ_dphi=None,
+                d_dJ_dv=None):
+    """Run nsteps and return (J, dJ/dalpha); gradients w.r.t. the start state go to the given device tensors."""
+    J, da = ctypes.c_double(), ctypes.c_double()
+    _check(load().prs_adjoint(sim, nsteps, observable, eps_smooth, ckpt_every, ctypes.byref(J), ctypes.byref(da),
+                              _ptr(d_dJ_dphi), _ptr(d_dJ_dv)), "prs_adjoint")
+    return J.value, da.value
+
+
 def prs_default_tblock(params: prs_params) -> int:
     rc = load().prs_default_tblock(ctypes.byref(params))
     if rc < 0:
@@ -322,3 +340,41 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+def observable_with_grad(shape, phi_init, v_init, nsteps, observable, eps_smooth=0.1, ckpt_every=64,
+                         precision=PRS_FP32, **kw):
+    """Differentiable J(phi after nsteps) as a torch.autograd.Function over (phi_init, v_init, alpha).
+
+    phi_init, v_init: CUDA tensors of the field's shape; the returned scalar tensor
+    backpropagates dJ/dphi_init, dJ/dv_init and dJ/dalpha (alpha is a 0-d tensor
+    holding the damping coefficient of Eq. 2) through prs_adjoint.
+    """
+    import torch
+
+    class _PRSObservable(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, phi0, v0, alpha):
+            sim = Sim(shape, precision=precision, alpha=float(alpha.item()), **kw)
+            sim.set_state(phi0.detach().cpu().numpy(), v0.detach().cpu().numpy(), 0)
+            gphi = torch.empty_like(phi0)
+            gv = torch.empty_like(v0)
+            J, dA = prs_adjoint(sim.handle, nsteps, observable, eps_smooth, ckpt_every, gphi, gv)
+            sim.close()
+            ctx.save_for_backward(gphi, gv)
+            ctx.dA = dA
+            ctx.alpha_device = alpha.device
+            return torch.tensor(J, dtype=torch.float64, device=phi0.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gphi, gv = ctx.saved_tensors
+            s = gJ.to(gphi.dtype)
+            galpha = (gJ.detach() * ctx.dA).to(device=ctx.alpha_device, dtype=torch.float64)
+            return gphi * s, gv * s, galpha
+
+    alpha = kw.pop("alpha_tensor", None)
+    if alpha is None:
+        import torch as _t
+        alpha = _t.tensor(kw.pop("alpha", 3.0), dtype=_t.float64, requires_grad=True)
+    return _PRSObservable.apply(phi_init, v_init, alpha)

@@ -11,32 +11,17 @@
 
 #include "prs.h"
 #include "prs_internal.h"
+#include "prs_sim.h"
 
 using namespace prs;
 
-struct prs_sim {
-    prs_params p;
-    Geo g;
-    size_t elem;         // bytes per value
-    cudaStream_t stream;
-    void* phi[2];        // ping-pong field buffers
-    void* dphi;          // velocity, updated in place
-    int cur;             // which phi[] holds phi^n
-    bool owned;          // library allocated phi[] and dphi
-    bool have_buffers;
-    bool initialised;
-    int64_t n;           // step index of the state
-    double rc[6];        // deta, 1/dx^2, 1/phi0^2, 2D, V0, phi0
-    DiagScratch scr;
-    DevStatus* d_status; // device: result, counter, error word
-    DevStatus* h_status; // pinned host copy
-};
+
 
 // ------------------------------------------------------------------ errors
 
 static thread_local char g_last_error[256] = "";
 
-static int cuda_fail(cudaError_t e, const char* what)
+int prs::cuda_fail(cudaError_t e, const char* what)
 {
     snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
     return PRS_ECUDA;
@@ -75,7 +60,7 @@ static const double kPi = 3.14159265358979323846;
 static double potential_height(const prs_params& p) { return kPi * kPi / (2.0 * p.W0 * p.W0); }
 
 // Eq. 6 and the force prefactor of Eq. 2 at step n, in FP64 on the host.
-static void step_coefficients(const prs_params& p, int64_t n, double out[5])
+void prs::step_coefficients(const prs_params& p, int64_t n, double out[5])
 {
     double eta = p.eta0 + (double)n * p.deta;  // computed from n, never accumulated
     double delta = 0.5 * p.alpha * p.deta * p.era_m / eta;
@@ -90,7 +75,7 @@ static void step_coefficients(const prs_params& p, int64_t n, double out[5])
 
 // Leapfrog stability of Eqs. 3-5 at step n: deta^2 (4D/dx^2 + max|V''|)/4 < 1,
 // with max|V''| = 2 cV over |phi| <= phi0.
-static bool cfl_ok(const prs_params& p, int64_t n)
+bool prs::cfl_ok(const prs_params& p, int64_t n)
 {
     double c[5];
     step_coefficients(p, n, c);
@@ -200,7 +185,7 @@ extern "C" int prs_bind(prs_sim* s, void* d_phi_a, void* d_phi_b, void* d_dphi)
     return PRS_OK;
 }
 
-static int ensure_buffers(prs_sim* s)
+int prs::ensure_buffers(prs_sim* s)
 {
     if (s->have_buffers) return PRS_OK;
     size_t bytes = (size_t)s->g.S * s->elem;
@@ -340,7 +325,7 @@ extern "C" int prs_step(prs_sim* s, int64_t nsteps)
 
 // After a synchronised read of h_status: a bounded device wait that gave up makes
 // the state untrustworthy; report it once and clear the word.
-static int check_device_error(prs_sim* s)
+int prs::check_device_error(prs_sim* s)
 {
     if (s->h_status->error == 0) return PRS_OK;
     snprintf(g_last_error, sizeof g_last_error, "device wait timed out (code %u)", s->h_status->error);

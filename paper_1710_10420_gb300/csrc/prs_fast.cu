@@ -16,7 +16,8 @@
 //    row is whole, so the periodic wrap is a shared-memory read by lanes 0/31);
 //    y and z neighbours are 128-bit shared-memory reads.
 //  * dphi is pointwise: each thread loads its float4 of the next plane into
-//    registers one plane ahead, and writes it back in place.
+//    registers one plane ahead, and writes it back (in place, or to a separate
+//    output buffer when the adjoint stores every state of a segment).
 //  * phi^{n+1} and dphi^{n+1/2} leave as coalesced 128-bit stores.
 // Every mbarrier wait is bounded (prs_ptx.cuh) and the decision to give up is
 // made block-wide, so a lost copy ends the kernel with an error code instead of
@@ -81,7 +82,7 @@ __device__ __noinline__ void drain(uint64_t* bar, int from, int issued, unsigned
 
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
-    k_step3d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, float* __restrict__ v, int nx,
+    k_step3d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out, int nx,
                  int ny, int nz, int ty, int cz, StepCoef<float> k, RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
         const float* pc = ring + ((zi + 1) & 3) * tile + nx;
         const float* pp = ring + ((zi + 2) & 3) * tile + nx;
         float* po = phi_out + (size_t)z * plane + (size_t)y0 * nx;
-        float* vo = v + (size_t)z * plane + (size_t)y0 * nx;
+        float* vo = v_out + (size_t)z * plane + (size_t)y0 * nx;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int off = row[j] * nx + 4 * col[j];
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
 // (band 0 = the row above the chunk, band nb+1 = the row below it).
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
-    k_step2d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, float* __restrict__ v, int nx,
+    k_step2d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out, int nx,
                  int ny, int rb, int cy, StepCoef<float> k, RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
             update4(c, left, right, yp, ym, ym, ym, vc[j], pn, k, rc, false);
             const size_t off = (size_t)(yb + row[j]) * nx + 4 * col[j];
             stg4(phi_out + off, pn);
-            stg4(v + off, vc[j]);
+            stg4(v_out + off, vc[j]);
         }
         if (bi + 1 < nb) {
 #pragma unroll
@@ -717,8 +718,8 @@ static int sm_count()
     return n;
 }
 
-cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, float* v, StepCoef<float> k,
-                             RunConst<float> rc, unsigned int* err, cudaStream_t st)
+cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
+                             StepCoef<float> k, RunConst<float> rc, unsigned int* err, cudaStream_t st)
 {
     static bool attr3 = false, attr2 = false;
     const int t = kItems * 1024 / g.nx;
@@ -736,8 +737,8 @@ cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, float* v
         int nchunks = pick_chunks(ytiles, g.nz, 16, slots);
         const int cz = (g.nz + nchunks - 1) / nchunks;
         nchunks = (g.nz + cz - 1) / cz;
-        k_step3d_f32<kItems><<<ytiles * nchunks, kFastThreads, sm, st>>>(in, out, v, g.nx, g.ny, g.nz, t, cz, k, rc,
-                                                                         err);
+        k_step3d_f32<kItems><<<ytiles * nchunks, kFastThreads, sm, st>>>(in, out, v, v_out, g.nx, g.ny, g.nz, t, cz,
+                                                                         k, rc, err);
         return cudaGetLastError();
     }
     const size_t sm = smem2d(g.nx, t);
@@ -753,7 +754,7 @@ cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, float* v
     const int bpc = (bands + nchunks - 1) / nchunks;
     const int cy = bpc * t;
     nchunks = (g.ny + cy - 1) / cy;
-    k_step2d_f32<kItems><<<nchunks, kFastThreads, sm, st>>>(in, out, v, g.nx, g.ny, t, cy, k, rc, err);
+    k_step2d_f32<kItems><<<nchunks, kFastThreads, sm, st>>>(in, out, v, v_out, g.nx, g.ny, t, cy, k, rc, err);
     return cudaGetLastError();
 }
 

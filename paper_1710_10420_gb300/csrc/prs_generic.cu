@@ -80,8 +80,8 @@ __device__ __forceinline__ void site_update(R c, R xp, R xm, R yp, R ym, R zp, R
 }
 
 template <typename R, bool REPRO, int D>
-__global__ void k_step_generic(const R* __restrict__ phi, R* __restrict__ phi_out, R* __restrict__ dphi, Geo g,
-                               StepCoef<R> k, RunConst<R> rc)
+__global__ void k_step_generic(const R* __restrict__ phi, R* __restrict__ phi_out, const R* dphi, R* dphi_out,
+                               Geo g, StepCoef<R> k, RunConst<R> rc)
 {
     const int64_t nx = g.nx, ny = g.ny, nz = g.nz;
     const int64_t plane = nx * ny;
@@ -106,7 +106,7 @@ __global__ void k_step_generic(const R* __restrict__ phi, R* __restrict__ phi_ou
         R v = dphi[s];
         R pn;
         site_update<R, REPRO, D>(c, xp, xm, yp, ym, zp, zm, v, pn, k, rc);
-        dphi[s] = v;
+        dphi_out[s] = v;
         phi_out[s] = pn;
     }
 }
@@ -118,26 +118,28 @@ static RunConst<R> make_rc(const double rcd[6])
 }
 
 template <typename R, bool REPRO>
-static cudaError_t step_generic_t(const Geo& g, const void* in, void* out, void* dphi, double c1, double c2, double cV,
-                                  const double rcd[6], cudaStream_t st)
+static cudaError_t step_generic_t(const Geo& g, const void* in, void* out, const void* dphi, void* dphi_out, double c1,
+                                  double c2, double cV, const double rcd[6], cudaStream_t st)
 {
     const int block = 256;
     int grid = grid_for(g.S, block);
     StepCoef<R> k{(R)c1, (R)c2, (R)cV};
     RunConst<R> rc = make_rc<R>(rcd);
     if (g.dims == 3)
-        k_step_generic<R, REPRO, 3><<<grid, block, 0, st>>>((const R*)in, (R*)out, (R*)dphi, g, k, rc);
+        k_step_generic<R, REPRO, 3><<<grid, block, 0, st>>>((const R*)in, (R*)out, (const R*)dphi, (R*)dphi_out, g, k,
+                                                             rc);
     else
-        k_step_generic<R, REPRO, 2><<<grid, block, 0, st>>>((const R*)in, (R*)out, (R*)dphi, g, k, rc);
+        k_step_generic<R, REPRO, 2><<<grid, block, 0, st>>>((const R*)in, (R*)out, (const R*)dphi, (R*)dphi_out, g, k,
+                                                             rc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const void* in, void* out, void* dphi,
-                                double c1, double c2, double cV, const double rcd[6], cudaStream_t st)
+cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const void* in, void* out, const void* dphi,
+                                void* dphi_out, double c1, double c2, double cV, const double rcd[6], cudaStream_t st)
 {
-    if (precision == PRS_FP32) return step_generic_t<float, false>(g, in, out, dphi, c1, c2, cV, rcd, st);
-    if (repro) return step_generic_t<double, true>(g, in, out, dphi, c1, c2, cV, rcd, st);
-    return step_generic_t<double, false>(g, in, out, dphi, c1, c2, cV, rcd, st);
+    if (precision == PRS_FP32) return step_generic_t<float, false>(g, in, out, dphi, dphi_out, c1, c2, cV, rcd, st);
+    if (repro) return step_generic_t<double, true>(g, in, out, dphi, dphi_out, c1, c2, cV, rcd, st);
+    return step_generic_t<double, false>(g, in, out, dphi, dphi_out, c1, c2, cV, rcd, st);
 }
 
 // ------------------------------------------------------------ diagnostics

@@ -69,6 +69,11 @@ cudaError_t launch_step(const Geo& g, int precision, bool repro, const void* phi
                         const double* c1, const double* c2, const double* cV, int nsteps_in_pass,
                         const double run_const[6], unsigned int* err, cudaStream_t st);
 
+// As launch_step with dphi read from dphi_in and written to dphi_out (may be equal).
+cudaError_t launch_step_io(const Geo& g, int precision, bool repro, const void* phi_in, void* phi_out,
+                           const void* dphi_in, void* dphi_out, const double* c1, const double* c2, const double* cV,
+                           int nsteps_in_pass, const double run_const[6], unsigned int* err, cudaStream_t st);
+
 // Largest number of steps one launch_step pass can fuse for this geometry/precision.
 int max_fused_steps(const Geo& g, int precision, bool repro);
 

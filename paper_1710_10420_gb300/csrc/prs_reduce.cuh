@@ -44,6 +44,8 @@ __device__ __forceinline__ void block_reduce_and_finish(DiagAcc a, const DiagScr
 {
     __shared__ DiagAcc warp_sums[32];
     __shared__ bool is_last;
+    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
     acc_warp_reduce(a);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) warp_sums[wid] = a;
@@ -52,10 +54,10 @@ __device__ __forceinline__ void block_reduce_and_finish(DiagAcc a, const DiagScr
         DiagAcc b = lane < nw ? warp_sums[lane] : DiagAcc{0.0, 0.0, 0, 0, 0, 0};
         acc_warp_reduce(b);
         if (lane == 0) {
-            scr.partials[blockIdx.x] = b;
+            scr.partials[bid] = b;
             __threadfence();
             unsigned int done = atomicAdd(scr.counter, 1u);
-            is_last = (done == gridDim.x - 1);
+            is_last = (done == nblocks - 1);
         }
     }
     __syncthreads();
@@ -64,7 +66,7 @@ __device__ __forceinline__ void block_reduce_and_finish(DiagAcc a, const DiagScr
     __threadfence();
     if (wid == 0) {
         DiagAcc t{0.0, 0.0, 0, 0, 0, 0};
-        for (int i = lane; i < (int)gridDim.x; i += 32) {
+        for (int i = lane; i < (int)nblocks; i += 32) {
             // other blocks wrote these: read through L2, not a possibly stale L1 line
             const DiagAcc* q = scr.partials + i;
             DiagAcc p{__ldcg(&q->sum_w), __ldcg(&q->sum_ratio), __ldcg(&q->n_links),

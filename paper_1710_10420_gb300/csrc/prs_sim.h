@@ -1,0 +1,41 @@
+// prs_sim.h -- the run object behind the opaque prs_sim handle (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "prs.h"
+#include "prs_internal.h"
+
+struct prs_sim {
+    prs_params p;
+    prs::Geo g;
+    size_t elem;         // bytes per value
+    cudaStream_t stream;
+    void* phi[2];        // ping-pong field buffers
+    void* dphi;          // velocity, updated in place
+    int cur;             // which phi[] holds phi^n
+    bool owned;          // library allocated phi[] and dphi
+    bool have_buffers;
+    bool initialised;
+    int64_t n;           // step index of the state
+    double rc[6];        // deta, 1/dx^2, 1/phi0^2, 2D, V0, phi0
+    prs::DiagScratch scr;
+    prs::DevStatus* d_status; // device: result, counter, error word
+    prs::DevStatus* h_status; // pinned host copy
+};
+
+namespace prs {
+
+// FP64 step-n coefficients: c1, c2, cV, delta, d delta / d alpha (Eq. 4, Eq. 6).
+void step_coefficients(const prs_params& p, int64_t n, double out[5]);
+// Leapfrog stability at step n.
+bool cfl_ok(const prs_params& p, int64_t n);
+// Record a CUDA error for prs_last_error(); returns PRS_ECUDA.
+int cuda_fail(cudaError_t e, const char* what);
+// Allocate the field buffers if none are bound or allocated yet.
+int ensure_buffers(prs_sim* s);
+// After a synchronised read of s->h_status: PRS_ETIMEOUT (once) if a device wait gave up.
+int check_device_error(prs_sim* s);
+
+}  // namespace prs

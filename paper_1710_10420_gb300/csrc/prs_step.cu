@@ -3,10 +3,10 @@
 
 namespace prs {
 
-cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const void* in, void* out, void* dphi,
-                                double c1, double c2, double cV, const double rcd[6], cudaStream_t st);
-cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, float* v, StepCoef<float> k,
-                             RunConst<float> rc, unsigned int* err, cudaStream_t st);
+cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const void* in, void* out, const void* dphi,
+                                void* dphi_out, double c1, double c2, double cV, const double rcd[6], cudaStream_t st);
+cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
+                             StepCoef<float> k, RunConst<float> rc, unsigned int* err, cudaStream_t st);
 
 int max_fused_steps(const Geo& g, int precision, bool repro)
 {
@@ -20,14 +20,24 @@ cudaError_t launch_step(const Geo& g, int precision, bool repro, const void* phi
                         const double* c1, const double* c2, const double* cV, int nsteps_in_pass,
                         const double run_const[6], unsigned int* err, cudaStream_t st)
 {
+    return launch_step_io(g, precision, repro, phi_in, phi_out, dphi, dphi, c1, c2, cV, nsteps_in_pass, run_const,
+                          err, st);
+}
+
+cudaError_t launch_step_io(const Geo& g, int precision, bool repro, const void* phi_in, void* phi_out,
+                           const void* dphi_in, void* dphi_out, const double* c1, const double* c2, const double* cV,
+                           int nsteps_in_pass, const double run_const[6], unsigned int* err, cudaStream_t st)
+{
     if (nsteps_in_pass != 1) return cudaErrorInvalidValue;
     if (fast_step_ok(g, precision)) {
         StepCoef<float> k{(float)c1[0], (float)c2[0], (float)cV[0]};
         RunConst<float> rc{(float)run_const[0], (float)run_const[1], (float)run_const[2], (float)run_const[3],
                            (float)run_const[4], (float)run_const[5]};
-        return launch_step_fast(g, (const float*)phi_in, (float*)phi_out, (float*)dphi, k, rc, err, st);
+        return launch_step_fast(g, (const float*)phi_in, (float*)phi_out, (const float*)dphi_in, (float*)dphi_out, k,
+                                rc, err, st);
     }
-    return launch_step_generic(g, precision, repro, phi_in, phi_out, dphi, c1[0], c2[0], cV[0], run_const, st);
+    return launch_step_generic(g, precision, repro, phi_in, phi_out, dphi_in, dphi_out, c1[0], c2[0], cV[0], run_const,
+                               st);
 }
 
 }  // namespace prs
