@@ -165,6 +165,44 @@ int prs_measure_noalloc(const prs_params* params, const void* d_phi, const void*
 /* Release the run and the memory the library allocated for it (not bound buffers). */
 int prs_destroy(prs_sim* sim);
 
+/* --------------------------------------------------------------- ensembles
+ * Many independent runs (the paper's sets of realisations, Sec. III) advanced by
+ * one persistent kernel: every run is cut into tiles and the work items
+ * (run, tile, step) are taken in an order in which each item only waits, with a
+ * bounded spin, for items already taken; diagnostics are fused into the steps
+ * that read the same state.  Runs must be FP32 with an x side that is a multiple
+ * of 128 dividing 4096 (3D: at most 1024) and 4096/x dividing the y side. */
+
+/* Create an ensemble of nruns runs (each validated as by prs_create), allocate all
+ * fields, pick tile lengths and the L2 grouping by timing short trials on them
+ * (the autotuner), then set every run to its seeded random initial condition
+ * (step 0).  stream may be NULL (the ensemble then creates its own stream). */
+int prs_batch_create(const prs_params* runs, int nruns, void* stream, prs_batch** out);
+
+/* Advance run r by nsteps_per_run[r] (>= 0) steps in one persistent launch.  With
+ * measure_every > 0, the diagnostics of run r at its steps n, n+m, ... (n its
+ * step at the call, up to n + nsteps_per_run[r]) are written to
+ *   out_series[(r*out_capacity + k)*4 + {0,1,2,3}] = {step, A/V, gamma v, n_links}
+ * (FP64 reduction, Eq. 7 and Eq. 8); out_capacity must be at least
+ * nsteps_per_run[r]/measure_every + 1 for every run.  Synchronises.  Returns
+ * PRS_ETIMEOUT if a bounded wait in the kernel gave up (the fields are then not
+ * trustworthy). */
+int prs_batch_run(prs_batch* batch, const int64_t* nsteps_per_run, int64_t measure_every, double* out_series,
+                  int64_t out_capacity);
+
+/* Host copies of run `run`'s fields (either may be NULL) and its step index. */
+int prs_batch_get_state(prs_batch* batch, int run, void* h_phi, void* h_dphi, int64_t* n);
+
+/* Overwrite run `run`'s fields from host arrays and set its step index. */
+int prs_batch_set_state(prs_batch* batch, int run, const void* h_phi, const void* h_dphi, int64_t n);
+
+/* The autotuner's choice: tile length of `run` (bands of 4096/x rows in 2D,
+ * z-planes in 3D) and the bytes of fields per L2 group. */
+int prs_batch_tuning(prs_batch* batch, int run, int* tile_len, double* group_bytes);
+
+/* Release the ensemble and everything it allocated. */
+int prs_batch_destroy(prs_batch* batch);
+
 /* ---------------------------------------------------------------- adjoint
  * Not in the paper: gradients of a smooth stand-in for the wall diagnostics
  * (PRS_OBS_GRAD_ENERGY or PRS_OBS_SMOOTH_AREA with smoothing width eps_smooth),

@@ -113,6 +113,12 @@ _SIGS = {
     "prs_destroy": (ctypes.c_int, [_VP]),
     "prs_coefficients": (ctypes.c_int, [_P, ctypes.c_int64, _DP]),
     "prs_default_tblock": (ctypes.c_int, [_P]),
+    "prs_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
+    "prs_batch_run": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64, _DP, ctypes.c_int64]),
+    "prs_batch_get_state": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _I64P]),
+    "prs_batch_set_state": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int64]),
+    "prs_batch_tuning": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP]),
+    "prs_batch_destroy": (ctypes.c_int, [_VP]),
     "prs_observable": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, _DP]),
     "prs_adjoint": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _DP, _DP, _VP,
                                    _VP]),
@@ -255,6 +261,46 @@ def prs_adjoint(sim, nsteps: int, observable: int, eps_smooth: float = 0.1, ckpt
     _check(load().prs_adjoint(sim, nsteps, observable, eps_smooth, ckpt_every, ctypes.byref(J), ctypes.byref(da),
                               _ptr(d_dJ_dphi), _ptr(d_dJ_dv)), "prs_adjoint")
     return J.value, da.value
+
+
+def prs_batch_create(runs, stream=None) -> ctypes.c_void_p:
+    """runs: a sequence of prs_params."""
+    arr = (prs_params * len(runs))(*runs)
+    h = _VP()
+    _check(load().prs_batch_create(arr, len(runs), stream, ctypes.byref(h)), "prs_batch_create")
+    return h
+
+
+def prs_batch_run(batch, nsteps_per_run, measure_every: int = 0, out_capacity: int = 0):
+    """Returns the diagnostic series as a numpy array [run][output][4] (step, A/V, gamma v, n_links)."""
+    ns = np.ascontiguousarray(nsteps_per_run, dtype=np.int64)
+    out = np.zeros((len(ns), max(out_capacity, 1), 4))
+    _check(load().prs_batch_run(batch, ns.ctypes.data_as(_I64P), measure_every,
+                                out.ctypes.data_as(_DP) if measure_every > 0 else None, out_capacity),
+           "prs_batch_run")
+    return out
+
+
+def prs_batch_get_state(batch, run: int, h_phi=None, h_dphi=None) -> int:
+    n = ctypes.c_int64()
+    _check(load().prs_batch_get_state(batch, run, _ptr(h_phi), _ptr(h_dphi), ctypes.byref(n)), "prs_batch_get_state")
+    return n.value
+
+
+def prs_batch_set_state(batch, run: int, h_phi, h_dphi, n: int) -> None:
+    phi = np.ascontiguousarray(h_phi, dtype=np.float32)  # kept alive across the call
+    dphi = np.ascontiguousarray(h_dphi, dtype=np.float32)
+    _check(load().prs_batch_set_state(batch, run, _ptr(phi), _ptr(dphi), n), "prs_batch_set_state")
+
+
+def prs_batch_tuning(batch, run: int):
+    t, g = ctypes.c_int(), ctypes.c_double()
+    _check(load().prs_batch_tuning(batch, run, ctypes.byref(t), ctypes.byref(g)), "prs_batch_tuning")
+    return t.value, g.value
+
+
+def prs_batch_destroy(batch) -> None:
+    _check(load().prs_batch_destroy(batch), "prs_batch_destroy")
 
 
 def prs_default_tblock(params: prs_params) -> int:

@@ -1,84 +1,19 @@
-// prs_fast.cu -- the FP32 leapfrog step (Eqs. 3-6) for boxes whose x side is a
-// multiple of 128 and at most 4096: the path the benchmark times.
-//
-// Design (GB300-first; the paper's OpenCL code ran one kernel per Eq. 3, 4, 5 with
-// no tiling): one kernel applies Eqs. 3-5 in a single pass over HBM, reading phi
-// and dphi once and writing them once (16 B per site-update).
-//
-//  * A CTA owns full x-rows.  In 3D it owns `ty` rows of y and a chunk of z-planes
-//    and marches along z; in 2D it owns a chunk of rows and marches along y.
-//  * phi arrives through the TMA engine: cp.async.bulk copies of whole row runs
-//    into a 4-slot shared-memory ring (3D: one slot = ty rows + the two y-halo
-//    rows of one z-plane; 2D: one slot = one band of rows), completion tracked by
-//    one mbarrier per slot.  While plane z is computed, planes z-1, z, z+1 are
-//    resident and plane z+2 is in flight.
-//  * x neighbours come from the neighbouring lane's float4 by warp shuffle (the
-//    row is whole, so the periodic wrap is a shared-memory read by lanes 0/31);
-//    y and z neighbours are 128-bit shared-memory reads.
-//  * dphi is pointwise: each thread loads its float4 of the next plane into
-//    registers one plane ahead, and writes it back (in place, or to a separate
-//    output buffer when the adjoint stores every state of a segment).
-//  * phi^{n+1} and dphi^{n+1/2} leave as coalesced 128-bit stores.
-// Every mbarrier wait is bounded (prs_ptx.cuh) and the decision to give up is
-// made block-wide, so a lost copy ends the kernel with an error code instead of
-// a hang.
+// prs_fast.cu -- the FP32 leapfrog step (Eqs. 3-6) and wall diagnostics (Eqs. 7, 8)
+// for boxes whose x side is a multiple of 128 and at most 4096 (3D: 1024): the
+// path the benchmark times.  One kernel applies Eqs. 3-5 in a single pass over
+// HBM (read phi and dphi once, write them once: 16 B per site-update), where the
+// paper's OpenCL code ran one kernel per equation.  The tile routines (bulk-async
+// plane staging, shuffles, bounded waits) live in prs_tile.cuh; this file sizes
+// the grids: one CTA per tile, two resident per SM.
 #include <cuda_runtime.h>
 
 #include "prs_arith.cuh"
 #include "prs_internal.h"
 #include "prs_ptx.cuh"
 #include "prs_reduce.cuh"
+#include "prs_tile.cuh"
 
 namespace prs {
-
-static constexpr int kFastThreads = 256;
-
-__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-
-__device__ __forceinline__ float4 ldg_stream4(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
-
-__device__ __forceinline__ void stg4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-
-// Eqs. 3-5 for the four sites of one float4, in the canonical order of site_update.
-__device__ __forceinline__ void update4(float4 c, float left, float right, float4 yp, float4 ym, float4 zp, float4 zm,
-                                        float4& v, float4& pn, const StepCoef<float>& k, const RunConst<float>& rc,
-                                        bool three_d)
-{
-    auto one = [&](float cc, float xp, float xm, float a, float b, float e, float f, float& vv) -> float {
-        float s2 = xp + xm;
-        s2 = s2 + (a + b);
-        if (three_d) s2 = s2 + (e + f);
-        float lap = (s2 - rc.twoD * cc) * rc.inv_dx2;
-        float force = (k.cV * cc) * ((cc * cc) * rc.inv_phi0sq - 1.0f);
-        float vn = k.c1 * vv + k.c2 * (lap - force);
-        vv = vn;
-        return cc + rc.deta * vn;
-    };
-    pn.x = one(c.x, c.y, left, yp.x, ym.x, zp.x, zm.x, v.x);
-    pn.y = one(c.y, c.z, c.x, yp.y, ym.y, zp.y, zm.y, v.y);
-    pn.z = one(c.z, c.w, c.y, yp.z, ym.z, zp.z, zm.z, v.z);
-    pn.w = one(c.w, right, c.z, yp.w, ym.w, zp.w, zm.w, v.w);
-}
-
-// x-neighbours of a float4 at column `col` of a whole row in shared memory.
-__device__ __forceinline__ void x_halo(const float* row, int col, int nq, int nx, int lane, float4 c, float& left,
-                                       float& right)
-{
-    left = __shfl_up_sync(0xffffffffu, c.w, 1);
-    right = __shfl_down_sync(0xffffffffu, c.x, 1);
-    if (lane == 0) left = row[col == 0 ? nx - 1 : 4 * col - 1];
-    if (lane == 31) right = row[col == nq - 1 ? 0 : 4 * col + 4];
-}
-
-// After a wait gave up: let the copies this CTA issued land (each wait again
-// bounded) before the CTA exits and its shared memory is reused.  Slots are
-// waited in issue order from local index `from`.
-__device__ __noinline__ void drain(uint64_t* bar, int from, int issued, unsigned int* err)
-{
-    for (int i = from; i <= issued; ++i) mbar_wait(&bar[i & 3], (i >> 2) & 1, err);
-}
-
-// ------------------------------------------------------------------------ 3D
 
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
@@ -86,349 +21,24 @@ __global__ void __launch_bounds__(kFastThreads, 2)
                  int ny, int nz, int ty, int cz, StepCoef<float> k, RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    float* ring = reinterpret_cast<float*>(smem_raw + 128);
-    const int tid = threadIdx.x, lane = tid & 31;
     const int ytiles = ny / ty;
-    const int y0 = (blockIdx.x % ytiles) * ty;
-    const int z0 = (blockIdx.x / ytiles) * cz;
-    const int zn = min(cz, nz - z0);
-    const int nq = nx >> 2;
-    const int tile = (ty + 2) * nx;
-    const size_t plane = (size_t)nx * ny;
-
-    if (tid == 0) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-
-    const int ytop = (y0 == 0 ? ny : y0) - 1;
-    const int ybot = (y0 + ty == ny) ? 0 : y0 + ty;
-    const unsigned rowb = (unsigned)nx * 4u;
-    const int nloc = zn + 2;  // local planes 0..zn+1 = global z0-1 .. z0+zn (periodic)
-    auto issue = [&](int i) {
-        int p = z0 - 1 + i;
-        p = p < 0 ? p + nz : (p >= nz ? p - nz : p);
-        float* dst = ring + (i & 3) * tile;
-        const float* src = phi_in + (size_t)p * plane;
-        uint64_t* b = &bar[i & 3];
-        mbar_arrive_expect_tx(b, rowb * (unsigned)(ty + 2));
-        bulk_g2s(dst, src + (size_t)ytop * nx, rowb, b);
-        bulk_g2s(dst + nx, src + (size_t)y0 * nx, rowb * (unsigned)ty, b);
-        bulk_g2s(dst + (size_t)(ty + 1) * nx, src + (size_t)ybot * nx, rowb, b);
-    };
-    int issued = -1;  // thread 0: highest local plane whose copy was issued
-    if (tid == 0)
-        for (int i = 0; i < 3 && i < nloc; ++i) issue(i), issued = i;
-
-    int row[ITEMS], col[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        int q = tid + kFastThreads * j;
-        row[j] = q / nq;
-        col[j] = q - row[j] * nq;
-    }
-    float4 vc[ITEMS];
-    {
-        const float* vb = v + (size_t)z0 * plane + (size_t)y0 * nx;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) vc[j] = ldg_stream4(vb + (size_t)row[j] * nx + 4 * col[j]);
-    }
-
-    for (int zi = 0; zi < zn; ++zi) {
-        // local planes zi, zi+1, zi+2 (= z-1, z, z+1) must be resident
-        bool ok = true;
-        if (zi == 0) ok = mbar_wait(&bar[0], 0, err) && mbar_wait(&bar[1], 0, err);
-        ok = ok && mbar_wait(&bar[(zi + 2) & 3], ((zi + 2) >> 2) & 1, err);
-        // block-wide decision; also: every thread is done with the previous plane
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) drain(bar, zi, issued, err);
-            return;
-        }
-        if (tid == 0 && zi + 3 < nloc) issue(zi + 3), issued = zi + 3;  // into the slot of plane z-2
-
-        const int z = z0 + zi;
-        float4 vn[ITEMS];
-        if (zi + 1 < zn) {
-            const float* vb = v + (size_t)(z + 1) * plane + (size_t)y0 * nx;
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vn[j] = ldg_stream4(vb + (size_t)row[j] * nx + 4 * col[j]);
-        }
-        const float* pm = ring + (zi & 3) * tile + nx;
-        const float* pc = ring + ((zi + 1) & 3) * tile + nx;
-        const float* pp = ring + ((zi + 2) & 3) * tile + nx;
-        float* po = phi_out + (size_t)z * plane + (size_t)y0 * nx;
-        float* vo = v_out + (size_t)z * plane + (size_t)y0 * nx;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int off = row[j] * nx + 4 * col[j];
-            const float* crow = pc + row[j] * nx;
-            float4 c = lds4(pc + off);
-            float4 ym = lds4(pc + off - nx);
-            float4 yp = lds4(pc + off + nx);
-            float4 zm = lds4(pm + off);
-            float4 zp = lds4(pp + off);
-            float left, right;
-            x_halo(crow, col[j], nq, nx, lane, c, left, right);
-            float4 pn;
-            update4(c, left, right, yp, ym, zp, zm, vc[j], pn, k, rc, true);
-            stg4(po + off, pn);
-            stg4(vo + off, vc[j]);
-        }
-        if (zi + 1 < zn) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];
-        }
-    }
+    Tile3D T{phi_in, phi_out, v, v_out, nx, ny, nz, ty, (int)(blockIdx.x % ytiles) * ty,
+             (int)(blockIdx.x / ytiles) * cz, 0};
+    T.zn = min(cz, nz - T.z0);
+    SiteAcc a{};
+    tile3d<ITEMS, true, false>(T, k, rc, smem_raw, nullptr, a, err);
 }
 
-// ------------------------------------------------------------------------ 2D
-
-// Bands of rb = ITEMS*1024/nx rows; slot i&3 of the ring holds band i of the chunk
-// (band 0 = the row above the chunk, band nb+1 = the row below it).
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
     k_step2d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out, int nx,
                  int ny, int rb, int cy, StepCoef<float> k, RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    float* ring = reinterpret_cast<float*>(smem_raw + 128);
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int y0 = blockIdx.x * cy;
-    const int yn = min(cy, ny - y0);
-    const int nb = yn / rb;
-    const int nq = nx >> 2;
-    const int slot = rb * nx;
-    const int ringrows = 4 * rb;
-    const unsigned rowb = (unsigned)nx * 4u;
-
-    if (tid == 0) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-
-    const int nloc = nb + 2;
-    auto issue = [&](int i) {
-        float* dst = ring + (i & 3) * slot;
-        uint64_t* b = &bar[i & 3];
-        if (i == 0) {  // the row above the chunk, at the band's last row
-            int y = (y0 == 0 ? ny : y0) - 1;
-            mbar_arrive_expect_tx(b, rowb);
-            bulk_g2s(dst + (size_t)(rb - 1) * nx, phi_in + (size_t)y * nx, rowb, b);
-        } else if (i == nb + 1) {  // the row below the chunk, at the band's first row
-            int y = (y0 + yn == ny) ? 0 : y0 + yn;
-            mbar_arrive_expect_tx(b, rowb);
-            bulk_g2s(dst, phi_in + (size_t)y * nx, rowb, b);
-        } else {
-            int y = y0 + (i - 1) * rb;
-            mbar_arrive_expect_tx(b, rowb * (unsigned)rb);
-            bulk_g2s(dst, phi_in + (size_t)y * nx, rowb * (unsigned)rb, b);
-        }
-    };
-    int issued = -1;
-    if (tid == 0)
-        for (int i = 0; i < 3 && i < nloc; ++i) issue(i), issued = i;
-
-    int row[ITEMS], col[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        int q = tid + kFastThreads * j;
-        row[j] = q / nq;
-        col[j] = q - row[j] * nq;
-    }
-    float4 vc[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) vc[j] = ldg_stream4(v + (size_t)(y0 + row[j]) * nx + 4 * col[j]);
-
-    for (int bi = 0; bi < nb; ++bi) {
-        bool ok = true;
-        if (bi == 0) ok = mbar_wait(&bar[0], 0, err) && mbar_wait(&bar[1], 0, err);
-        ok = ok && mbar_wait(&bar[(bi + 2) & 3], ((bi + 2) >> 2) & 1, err);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) drain(bar, bi, issued, err);
-            return;
-        }
-        if (tid == 0 && bi + 3 < nloc) issue(bi + 3), issued = bi + 3;
-
-        const int yb = y0 + bi * rb;  // first row of this band
-        float4 vn[ITEMS];
-        if (bi + 1 < nb) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vn[j] = ldg_stream4(v + (size_t)(yb + rb + row[j]) * nx + 4 * col[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int lr = (bi + 1) * rb + row[j];  // local row of this site in ring order
-            const float* crow = ring + (size_t)(lr % ringrows) * nx;
-            const float* urow = ring + (size_t)((lr + ringrows - 1) % ringrows) * nx;
-            const float* drow = ring + (size_t)((lr + 1) % ringrows) * nx;
-            float4 c = lds4(crow + 4 * col[j]);
-            float4 ym = lds4(urow + 4 * col[j]);
-            float4 yp = lds4(drow + 4 * col[j]);
-            float left, right;
-            x_halo(crow, col[j], nq, nx, lane, c, left, right);
-            float4 pn;
-            update4(c, left, right, yp, ym, ym, ym, vc[j], pn, k, rc, false);
-            const size_t off = (size_t)(yb + row[j]) * nx + 4 * col[j];
-            stg4(phi_out + off, pn);
-            stg4(v_out + off, vc[j]);
-        }
-        if (bi + 1 < nb) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];
-        }
-    }
-}
-
-// --------------------------------------------------------------- diagnostics
-//
-// Eq. 7 and Eq. 8 on the same plane staging as the step: every site tests the
-// signs of its 2D neighbours (one float4 of 4 sites at a time, x neighbours by
-// shuffle); only sites with a crossing link (a few per cent) read the extra
-// neighbours of the link-midpoint gradient from shared memory.  Each thread keeps
-// its own FP64 sums and integer counts; prs_reduce.cuh finishes them in a fixed
-// order.
-
-// Per-thread sums.  The site terms of one plane (at most 16 sites x 3 links) are
-// added in FP32 and folded into the FP64 totals once per plane: GB300 issues FP64
-// at a small fraction of its FP32 rate, and a per-site FP64 add made the kernel
-// arithmetic-bound.  The FP32 plane partial of <= 48 terms in [0, 1] (weights) or
-// of the ratios keeps a relative error below 48 ulp.
-struct SiteAcc {
-    double sw, sr;
-    float pw, pr;  // current plane's partial sums
-    int nl, nw, nv0, nnf;
-    __device__ __forceinline__ void fold()
-    {
-        sw += (double)pw;
-        sr += (double)pr;
-        pw = 0.0f;
-        pr = 0.0f;
-    }
-};
-
-// |g| / sum_i |g_i| with the hardware reciprocal square root and reciprocal
-// (a few ulp; num > 0 because the link's own component is non-zero).
-__device__ __forceinline__ float link_weight3(float gx, float gy, float gz)
-{
-    float num = gx * gx;
-    num = num + gy * gy;
-    num = num + gz * gz;
-    float den = fabsf(gx);
-    den = den + fabsf(gy);
-    den = den + fabsf(gz);
-    return __fdividef(num * rsqrtf(num), den);
-}
-
-__device__ __forceinline__ float link_weight2(float gx, float gy)
-{
-    float num = gx * gx;
-    num = num + gy * gy;
-    float den = fabsf(gx);
-    den = den + fabsf(gy);
-    return __fdividef(num * rsqrtf(num), den);
-}
-
-// Bit e set when component e of the float4 is negative (the (phi < 0) rule; -0 is not).
-__device__ __forceinline__ unsigned negmask4(float4 a)
-{
-    return (a.x < 0.0f ? 1u : 0u) | (a.y < 0.0f ? 2u : 0u) | (a.z < 0.0f ? 4u : 0u) | (a.w < 0.0f ? 8u : 0u);
-}
-
-// Eq. 8 terms of the wall sites among the four (bit e of `wall`), FP32 factored
-// potential, hardware reciprocal; plus the exact count of non-finite values,
-// screened by one sum (a non-finite value makes it non-finite).
-__device__ __forceinline__ void wall_sites4(SiteAcc& a, unsigned wall, float4 c, float4 vv, const RunConst<float>& rc)
-{
-    const float cs[4] = {c.x, c.y, c.z, c.w};
-    const float vs[4] = {vv.x, vv.y, vv.z, vv.w};
-    const float screen = ((c.x + c.y) + (c.z + c.w)) + ((vv.x + vv.y) + (vv.z + vv.w));
-    if (!isfinite(screen)) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) a.nnf += (!isfinite(cs[e]) || !isfinite(vs[e])) ? 1 : 0;
-    }
-    a.nw += __popc(wall);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const float s = cs[e];
-        const float u = ((s - rc.phi0) * (s + rc.phi0)) * rc.inv_phi0sq;
-        const float V = (rc.V0 * u) * u;
-        const bool w = (wall >> e) & 1u;
-        const bool pos = V > 0.0f;
-        a.nv0 += (w && !pos) ? 1 : 0;
-        a.pr += (w && pos) ? __fdividef(vs[e] * vs[e], V) : 0.0f;
-    }
-}
-
-// Crossing links are compacted per warp: each lane appends its links (site e of
-// its float4, axis d) to the warp's queue in shared memory, then the warp takes
-// them 32 at a time, so the link-midpoint gradients cost one pass instead of one
-// divergent pass per site and axis.
-static constexpr int kQueuePerWarp = 32 * 12;  // 4 sites x 3 axes per lane
-static constexpr size_t kQueueBytes = (kFastThreads / 32) * kQueuePerWarp * sizeof(unsigned);
-
-// Appends this lane's set bits of `mask` (bit 4d+e: site e of the float4, axis d) to the warp queue;
-// returns the warp's total.
-__device__ __forceinline__ int enqueue_links(unsigned* wq, unsigned mask, int lane)
-{
-    const int cnt = __popc(mask);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    int k = incl - cnt;
-    while (mask) {
-        const int b = __ffs(mask) - 1;
-        mask &= mask - 1;
-        wq[k++] = ((unsigned)lane << 4) | (unsigned)b;
-    }
-    __syncwarp();
-    return total;
-}
-
-// Eq. 7 weight of the link from (x, row r) of plane Pc along axis d (3D).
-__device__ __forceinline__ float weight3(const float* Pm, const float* Pc, const float* Pp, int r, int x, int d,
-                                        int nx)
-{
-    const int xr = x + 1 == nx ? 0 : x + 1, xl = x == 0 ? nx - 1 : x - 1;
-    const float* cm = Pc + (r - 1) * nx;
-    const float* c0 = Pc + r * nx;
-    const float* c1 = Pc + (r + 1) * nx;
-    const float s = c0[x];
-    float gx, gy, gz;
-    if (d == 0) {  // to (x+1, y, z)
-        gx = c0[xr] - s;
-        gy = 0.25f * ((c1[x] - cm[x]) + (c1[xr] - cm[xr]));
-        gz = 0.25f * ((Pp[r * nx + x] - Pm[r * nx + x]) + (Pp[r * nx + xr] - Pm[r * nx + xr]));
-    } else if (d == 1) {  // to (x, y+1, z)
-        gx = 0.25f * ((c0[xr] - c0[xl]) + (c1[xr] - c1[xl]));
-        gy = c1[x] - s;
-        gz = 0.25f * ((Pp[r * nx + x] - Pm[r * nx + x]) + (Pp[(r + 1) * nx + x] - Pm[(r + 1) * nx + x]));
-    } else {  // to (x, y, z+1)
-        const float* p0 = Pp + r * nx;
-        gx = 0.25f * ((c0[xr] - c0[xl]) + (p0[xr] - p0[xl]));
-        gy = 0.25f * ((c1[x] - cm[x]) + (Pp[(r + 1) * nx + x] - Pp[(r - 1) * nx + x]));
-        gz = p0[x] - s;
-    }
-    return link_weight3(gx, gy, gz);
-}
-
-// Eq. 7 weight of the link from x of row crow along axis d (2D); urow/drow are
-// the rows above and below.
-__device__ __forceinline__ float weight2(const float* urow, const float* crow, const float* drow, int x, int d, int nx)
-{
-    const int xr = x + 1 == nx ? 0 : x + 1, xl = x == 0 ? nx - 1 : x - 1;
-    const float s = crow[x];
-    if (d == 0) return link_weight2(crow[xr] - s, 0.25f * ((drow[x] - urow[x]) + (drow[xr] - urow[xr])));
-    return link_weight2(0.25f * ((crow[xr] - crow[xl]) + (drow[xr] - drow[xl])), drow[x] - s);
+    Tile2D T{phi_in, phi_out, v, v_out, nx, ny, rb, (int)blockIdx.x * cy, 0};
+    T.yn = min(cy, ny - T.y0);
+    SiteAcc a{};
+    tile2d<ITEMS, true, false>(T, k, rc, smem_raw, nullptr, a, err);
 }
 
 template <int ITEMS>
@@ -437,115 +47,14 @@ __global__ void __launch_bounds__(kFastThreads, 2)
                     int cz, RunConst<float> rc, DiagScratch scr, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    float* ring = reinterpret_cast<float*>(smem_raw + 128);
-    const int tid = threadIdx.x, lane = tid & 31;
     const int ytiles = ny / ty;
-    const int y0 = (blockIdx.x % ytiles) * ty;
-    const int z0 = (blockIdx.x / ytiles) * cz;
-    const int zn = min(cz, nz - z0);
-    const int nq = nx >> 2;
-    const int tile = (ty + 2) * nx;
-    const size_t plane = (size_t)nx * ny;
-
-    if (tid == 0) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-
-    const int ytop = (y0 == 0 ? ny : y0) - 1;
-    const int ybot = (y0 + ty == ny) ? 0 : y0 + ty;
-    const unsigned rowb = (unsigned)nx * 4u;
-    const int nloc = zn + 2;
-    auto issue = [&](int i) {
-        int p = z0 - 1 + i;
-        p = p < 0 ? p + nz : (p >= nz ? p - nz : p);
-        float* dst = ring + (i & 3) * tile;
-        const float* src = phi + (size_t)p * plane;
-        uint64_t* b = &bar[i & 3];
-        mbar_arrive_expect_tx(b, rowb * (unsigned)(ty + 2));
-        bulk_g2s(dst, src + (size_t)ytop * nx, rowb, b);
-        bulk_g2s(dst + nx, src + (size_t)y0 * nx, rowb * (unsigned)ty, b);
-        bulk_g2s(dst + (size_t)(ty + 1) * nx, src + (size_t)ybot * nx, rowb, b);
-    };
-    int issued = -1;
-    if (tid == 0)
-        for (int i = 0; i < 3 && i < nloc; ++i) issue(i), issued = i;
-
-    int row[ITEMS], col[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        int q = tid + kFastThreads * j;
-        row[j] = q / nq;
-        col[j] = q - row[j] * nq;
-    }
+    Tile3D T{phi, nullptr, v, nullptr, nx, ny, nz, ty, (int)(blockIdx.x % ytiles) * ty,
+             (int)(blockIdx.x / ytiles) * cz, 0};
+    T.zn = min(cz, nz - T.z0);
+    unsigned* wq = reinterpret_cast<unsigned*>(smem_raw + tile_smem3d(nx, ty)) + (threadIdx.x >> 5) * kQueuePerWarp;
     SiteAcc a{0.0, 0.0, 0.0f, 0.0f, 0, 0, 0, 0};
-    unsigned* wq = reinterpret_cast<unsigned*>(ring + 4 * tile) + (tid >> 5) * kQueuePerWarp;
-    float4 vc[ITEMS];
-    {
-        const float* vb = v + (size_t)z0 * plane + (size_t)y0 * nx;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) vc[j] = ldg_stream4(vb + (size_t)row[j] * nx + 4 * col[j]);
-    }
-    for (int zi = 0; zi < zn; ++zi) {
-        bool ok = true;
-        if (zi == 0) ok = mbar_wait(&bar[0], 0, err) && mbar_wait(&bar[1], 0, err);
-        ok = ok && mbar_wait(&bar[(zi + 2) & 3], ((zi + 2) >> 2) & 1, err);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) drain(bar, zi, issued, err);
-            break;  // the partial sums still go through the block reduction
-        }
-        if (tid == 0 && zi + 3 < nloc) issue(zi + 3), issued = zi + 3;
-        const int z = z0 + zi;
-        float4 vn[ITEMS];
-        if (zi + 1 < zn) {
-            const float* vb = v + (size_t)(z + 1) * plane + (size_t)y0 * nx;
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vn[j] = ldg_stream4(vb + (size_t)row[j] * nx + 4 * col[j]);
-        }
-        const float* Pm = ring + (zi & 3) * tile + nx;
-        const float* Pc = ring + ((zi + 1) & 3) * tile + nx;
-        const float* Pp = ring + ((zi + 2) & 3) * tile + nx;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int r = row[j];
-            const int off = r * nx + 4 * col[j];
-            float4 c = lds4(Pc + off);
-            float4 ym4 = lds4(Pc + off - nx);
-            float4 yp4 = lds4(Pc + off + nx);
-            float4 zm4 = lds4(Pm + off);
-            float4 zp4 = lds4(Pp + off);
-            float left, right;
-            x_halo(Pc + r * nx, col[j], nq, nx, lane, c, left, right);
-            const unsigned sc = negmask4(c);
-            const unsigned sxp = (sc >> 1) | (right < 0.0f ? 8u : 0u);
-            const unsigned sxm = ((sc << 1) & 15u) | (left < 0.0f ? 1u : 0u);
-            const unsigned lx = sc ^ sxp, ly = sc ^ negmask4(yp4), lz = sc ^ negmask4(zp4);
-            const unsigned wall = lx | ly | lz | (sc ^ sxm) | (sc ^ negmask4(ym4)) | (sc ^ negmask4(zm4));
-            wall_sites4(a, wall, c, vc[j], rc);
-            // bit 4d+e: the link from site e along axis d crosses
-            const unsigned lmask = lx | (ly << 4) | (lz << 8);
-            a.nl += __popc(lmask);
-            const int total = enqueue_links(wq, lmask, lane);
-            const int colbase = col[j] - lane;  // the warp's 32 float4 are consecutive in one row
-            for (int base = 0; base < total; base += 32) {
-                const int idx = base + lane;
-                if (idx < total) {
-                    const unsigned ent = wq[idx];
-                    const int b = ent & 15, e = b & 3, d = b >> 2;
-                    a.pw += weight3(Pm, Pc, Pp, r, 4 * (colbase + (int)(ent >> 4)) + e, d, nx);
-                }
-            }
-            __syncwarp();
-        }
-        a.fold();
-        if (zi + 1 < zn) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];
-        }
-    }
+    StepCoef<float> k{};
+    tile3d<ITEMS, false, true>(T, k, rc, smem_raw, wq, a, err);  // on a timeout the partial sums still reduce
     block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
 }
 
@@ -555,111 +64,12 @@ __global__ void __launch_bounds__(kFastThreads, 2)
                     RunConst<float> rc, DiagScratch scr, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    float* ring = reinterpret_cast<float*>(smem_raw + 128);
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int y0 = blockIdx.x * cy;
-    const int yn = min(cy, ny - y0);
-    const int nb = yn / rb;
-    const int nq = nx >> 2;
-    const int slot = rb * nx;
-    const int ringrows = 4 * rb;
-    const unsigned rowb = (unsigned)nx * 4u;
-
-    if (tid == 0) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    const int nloc = nb + 2;
-    auto issue = [&](int i) {
-        float* dst = ring + (i & 3) * slot;
-        uint64_t* b = &bar[i & 3];
-        if (i == 0) {
-            int y = (y0 == 0 ? ny : y0) - 1;
-            mbar_arrive_expect_tx(b, rowb);
-            bulk_g2s(dst + (size_t)(rb - 1) * nx, phi + (size_t)y * nx, rowb, b);
-        } else if (i == nb + 1) {
-            int y = (y0 + yn == ny) ? 0 : y0 + yn;
-            mbar_arrive_expect_tx(b, rowb);
-            bulk_g2s(dst, phi + (size_t)y * nx, rowb, b);
-        } else {
-            int y = y0 + (i - 1) * rb;
-            mbar_arrive_expect_tx(b, rowb * (unsigned)rb);
-            bulk_g2s(dst, phi + (size_t)y * nx, rowb * (unsigned)rb, b);
-        }
-    };
-    int issued = -1;
-    if (tid == 0)
-        for (int i = 0; i < 3 && i < nloc; ++i) issue(i), issued = i;
-
-    int row[ITEMS], col[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        int q = tid + kFastThreads * j;
-        row[j] = q / nq;
-        col[j] = q - row[j] * nq;
-    }
+    Tile2D T{phi, nullptr, v, nullptr, nx, ny, rb, (int)blockIdx.x * cy, 0};
+    T.yn = min(cy, ny - T.y0);
+    unsigned* wq = reinterpret_cast<unsigned*>(smem_raw + tile_smem2d(nx, rb)) + (threadIdx.x >> 5) * kQueuePerWarp;
     SiteAcc a{0.0, 0.0, 0.0f, 0.0f, 0, 0, 0, 0};
-    unsigned* wq = reinterpret_cast<unsigned*>(ring + 4 * slot) + (tid >> 5) * kQueuePerWarp;
-    float4 vc[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) vc[j] = ldg_stream4(v + (size_t)(y0 + row[j]) * nx + 4 * col[j]);
-
-    for (int bi = 0; bi < nb; ++bi) {
-        bool ok = true;
-        if (bi == 0) ok = mbar_wait(&bar[0], 0, err) && mbar_wait(&bar[1], 0, err);
-        ok = ok && mbar_wait(&bar[(bi + 2) & 3], ((bi + 2) >> 2) & 1, err);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) drain(bar, bi, issued, err);
-            break;
-        }
-        if (tid == 0 && bi + 3 < nloc) issue(bi + 3), issued = bi + 3;
-        const int yb = y0 + bi * rb;
-        float4 vn[ITEMS];
-        if (bi + 1 < nb) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vn[j] = ldg_stream4(v + (size_t)(yb + rb + row[j]) * nx + 4 * col[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int lr = (bi + 1) * rb + row[j];
-            const float* crow = ring + (size_t)(lr % ringrows) * nx;
-            const float* urow = ring + (size_t)((lr + ringrows - 1) % ringrows) * nx;
-            const float* drow = ring + (size_t)((lr + 1) % ringrows) * nx;
-            float4 c = lds4(crow + 4 * col[j]);
-            float4 ym4 = lds4(urow + 4 * col[j]);
-            float4 yp4 = lds4(drow + 4 * col[j]);
-            float left, right;
-            x_halo(crow, col[j], nq, nx, lane, c, left, right);
-            const unsigned sc = negmask4(c);
-            const unsigned sxp = (sc >> 1) | (right < 0.0f ? 8u : 0u);
-            const unsigned sxm = ((sc << 1) & 15u) | (left < 0.0f ? 1u : 0u);
-            const unsigned lx = sc ^ sxp, ly = sc ^ negmask4(yp4);
-            const unsigned wall = lx | ly | (sc ^ sxm) | (sc ^ negmask4(ym4));
-            wall_sites4(a, wall, c, vc[j], rc);
-            // bit 4d+e: the link from site e along axis d crosses
-            const unsigned lmask = lx | (ly << 4);
-            a.nl += __popc(lmask);
-            const int total = enqueue_links(wq, lmask, lane);
-            const int colbase = col[j] - lane;
-            for (int base = 0; base < total; base += 32) {
-                const int idx = base + lane;
-                if (idx < total) {
-                    const unsigned ent = wq[idx];
-                    const int b = ent & 15, e = b & 3, d = b >> 2;
-                    a.pw += weight2(urow, crow, drow, 4 * (colbase + (int)(ent >> 4)) + e, d, nx);
-                }
-            }
-            __syncwarp();
-        }
-        a.fold();
-        if (bi + 1 < nb) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];
-        }
-    }
+    StepCoef<float> k{};
+    tile2d<ITEMS, false, true>(T, k, rc, smem_raw, wq, a, err);
     block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
 }
 
@@ -667,8 +77,8 @@ __global__ void __launch_bounds__(kFastThreads, 2)
 
 static constexpr int kItems = 4;  // float4 per thread per plane: 4096 sites per plane tile
 
-static size_t smem3d(int nx, int ty) { return 128 + 4 * (size_t)(ty + 2) * nx * sizeof(float); }
-static size_t smem2d(int nx, int rb) { return 128 + 4 * (size_t)rb * nx * sizeof(float); }
+static size_t smem3d(int nx, int ty) { return tile_smem3d(nx, ty); }
+static size_t smem2d(int nx, int rb) { return tile_smem2d(nx, rb); }
 
 static constexpr size_t kFastSmemMax = 100 * 1024;
 static constexpr size_t kMeasureSmemMax = kFastSmemMax + kQueueBytes;

@@ -176,6 +176,27 @@ __device__ R link_weight(const R* __restrict__ phi, const Geo& g, int64_t x, int
         num = A::add(num, A::mul(gg, gg));
         den = A::add(den, fabs(gg));
     }
+    // den > 0 (the link's own component is non-zero); if the squares underflow,
+    // rescale the components by den first
+    const R tiny = sizeof(R) == 4 ? (R)1e-30 : (R)1e-290;
+    if (!(num >= tiny)) {
+        R n2 = (R)0;
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+            R gg;
+            if (e == d) {
+                gg = A::sub(pt, ps);
+            } else {
+                int ex = (e == 0), ey = (e == 1), ez = (e == 2);
+                R gs = A::sub(fetch(phi, g, x + ex, y + ey, z + ez), fetch(phi, g, x - ex, y - ey, z - ez));
+                R gt = A::sub(fetch(phi, g, tx + ex, ty + ey, tz + ez), fetch(phi, g, tx - ex, ty - ey, tz - ez));
+                gg = A::mul((R)0.25, A::add(gs, gt));
+            }
+            const R r = A::div(gg, den);
+            n2 = A::add(n2, A::mul(r, r));
+        }
+        return A::sqrt(n2);
+    }
     return A::div(A::sqrt(num), den);
 }
 

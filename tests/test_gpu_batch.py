@@ -1,0 +1,156 @@
+"""The persistent ensemble engine (prs_batch_*) against the oracle and the single-run path.
+
+Every run of a mixed 2D/3D ensemble, each with its own seed, era and number of
+steps, must match the FP64 oracle to the FP32 field tolerance (1e-5 relative);
+the fused diagnostics at output steps must match the oracle's on fields where
+FP32 cannot move a sign (static walls), exactly in the counts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1710_10420_gb300 as prs
+import prs_inputs as inp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available()
+    prs.load(build=True)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+RUNS = [  # shape, era_m, seed, nsteps
+    ((256, 128), 1.0, 11, 23),
+    ((128, 128), 2.0, 12, 17),
+    ((512, 64), 1.0, 13, 0),
+    ((128, 32, 16), 2.0, 14, 19),
+    ((256, 32, 12), 1.0, 15, 11),
+    ((4096, 8), 2.0, 16, 7),
+    ((1024, 8, 6), 1.0, 17, 14),
+]
+
+
+def _params(shape, era, seed):
+    return prs.make_params(shape, precision=prs.PRS_FP32, era_m=era, seed=seed)
+
+
+def test_mixed_ensemble_matches_oracle():
+    b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd, _ in RUNS])
+    try:
+        ns = [n for *_, n in RUNS]
+        prs.prs_batch_run(b, ns)
+        for r, (shape, era, seed, n) in enumerate(RUNS):
+            fshape = tuple(reversed(shape))
+            phi = np.empty(fshape, np.float32)
+            v = np.empty(fshape, np.float32)
+            assert prs.prs_batch_get_state(b, r, phi, v) == n
+            p = oracle.Params(shape, era_m=era)
+            ophi, ov = oracle.step(p, *oracle.init_random(p, seed), n)
+            assert _rel(phi, ophi) <= 1e-5, (shape, n)
+            assert _rel(v, ov) <= 1e-5 if n else np.all(v == 0)
+        # a second call continues every run from where it stopped
+        prs.prs_batch_run(b, [5] * len(RUNS))
+        for r, (shape, era, seed, n) in enumerate(RUNS[:3]):
+            phi = np.empty(tuple(reversed(shape)), np.float32)
+            assert prs.prs_batch_get_state(b, r, phi, None) == n + 5
+            p = oracle.Params(shape, era_m=era)
+            ophi, _ = oracle.step(p, *oracle.init_random(p, seed), n + 5)
+            assert _rel(phi, ophi) <= 1e-5
+    finally:
+        prs.prs_batch_destroy(b)
+
+
+def test_fused_diagnostics_on_static_walls():
+    """Kink pairs stay put: every output must give the oracle's exact counts and A/V = 2/(N dx)."""
+    runs = [((256, 64), 0), ((128, 64, 16), 2), ((128, 128), 1)]
+    b = prs.prs_batch_create([_params(s, 1.0, 1) for s, _ in runs])
+    try:
+        fields = []
+        for r, (shape, axis) in enumerate(runs):
+            phi, v = inp.kink_pair(shape, 10.0, axis=axis)
+            prs.prs_batch_set_state(b, r, phi, v, 0)
+            fields.append((phi, v))
+        out = prs.prs_batch_run(b, [20, 20, 20], measure_every=5, out_capacity=5)
+        for r, (shape, axis) in enumerate(runs):
+            p = oracle.Params(shape)
+            phi, v = fields[r]
+            d0 = oracle.measure(p, phi, v)
+            N = shape[axis]
+            for k in range(5):
+                step, area, gv, nl = out[r, k]
+                assert step == 5 * k
+                assert nl == d0.n_links
+                assert area == pytest.approx(2.0 / N, rel=1e-6)  # hardware rsqrt/reciprocal: a few ulp per weight
+            assert out[r, 0, 2] == pytest.approx(d0.gamma_v, abs=1e-12)  # zero velocity at step 0
+    finally:
+        prs.prs_batch_destroy(b)
+
+
+def test_diagnostics_at_step_zero_random_fields():
+    runs = RUNS[:5]
+    b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd, _ in runs])
+    try:
+        out = prs.prs_batch_run(b, [0] * len(runs), measure_every=1, out_capacity=1)
+        for r, (shape, era, seed, _) in enumerate(runs):
+            p = oracle.Params(shape, era_m=era)
+            d = oracle.measure(p, *oracle.init_random(p, seed))
+            assert out[r, 0, 3] == d.n_links
+            assert out[r, 0, 1] == pytest.approx(d.area_per_volume, rel=1e-5)
+    finally:
+        prs.prs_batch_destroy(b)
+
+
+def test_batch_is_deterministic_and_matches_single_runs():
+    """Two fresh ensembles give identical bits; each run agrees with prs_step + prs_measure."""
+    runs = RUNS[:5]
+    ns = [12, 9, 10, 8, 13]
+    outs, states = [], []
+    for _ in range(2):
+        b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd, _ in runs])
+        outs.append(prs.prs_batch_run(b, ns, measure_every=4, out_capacity=4))
+        st = []
+        for r, (shape, *_rest) in enumerate(runs):
+            phi = np.empty(tuple(reversed(shape)), np.float32)
+            prs.prs_batch_get_state(b, r, phi, None)
+            st.append(phi)
+        states.append(st)
+        prs.prs_batch_destroy(b)
+    assert np.array_equal(outs[0], outs[1])
+    for a, c in zip(states[0], states[1]):
+        assert np.array_equal(a, c)
+    for r, (shape, era, seed, _) in enumerate(runs):
+        sim = prs.Sim(shape, precision=prs.PRS_FP32, era_m=era, seed=seed)
+        sim.init()
+        sim.step(ns[r])
+        phi, _, _ = sim.get_state()
+        sim.close()
+        assert _rel(phi, states[0][r].astype(np.float64)) <= 1e-6
+
+
+def test_autotuner_reports_a_choice():
+    b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd, _ in RUNS[:3]])
+    try:
+        for r in range(3):
+            t, g = prs.prs_batch_tuning(b, r)
+            assert t in (8, 16, 32, 64) and g > 0
+    finally:
+        prs.prs_batch_destroy(b)
+
+
+def test_batch_rejects_unsupported_runs():
+    import ctypes
+
+    p = [prs.make_params((130, 64))]  # x side not a multiple of 128
+    arr = (prs.prs_params * 1)(*p)
+    h = ctypes.c_void_p()
+    assert prs.load().prs_batch_create(arr, 1, None, ctypes.byref(h)) == prs.PRS_EINVAL

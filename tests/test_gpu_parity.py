@@ -217,6 +217,20 @@ def test_measure_parity(precision, shape):
         assert d["gamma_v"] == pytest.approx(od.gamma_v, rel=tol), name
 
 
+@pytest.mark.parametrize("shape", [(128, 64), (37, 23), (128, 32, 8), (13, 11, 9)])
+def test_measure_tiny_magnitudes(shape):
+    """Fields of size 1e-25 (normal FP32 numbers whose squares underflow) keep their weights."""
+    phi = (1e-25 * inp.random_signs(shape, seed=4)).astype(np.float32)
+    v = np.zeros_like(phi)
+    sim = prs.Sim(shape, precision=prs.PRS_FP32)
+    sim.set_state(phi, v, 0)
+    d = sim.measure()
+    sim.close()
+    od = oracle.measure(oracle.Params(shape), phi.astype(np.float64), v.astype(np.float64))
+    assert d["n_links"] == od.n_links and d["n_wall"] == od.n_wall
+    assert d["area_per_volume"] == pytest.approx(od.area_per_volume, rel=1e-5)
+
+
 def test_measure_nonfinite_and_empty():
     shape = (16, 16)
     sim = prs.Sim(shape, precision=prs.PRS_FP64)
