@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--tblock", type=int, default=0, help="fused steps per HBM pass (0: library default)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the ensemble (batched vs one-at-a-time) figure")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward time figure")
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="fraction of each ensemble run's steps (1.0: every run to eta = N/2)")
     return ap.parse_args()
 
 
@@ -313,6 +317,10 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": args.steps * (len(passes) + 1),
     }
     sim.close()
+    if rank == 0 and not args.no_batch:
+        line["batch"] = run_batch_figure(prs, stream, dev, args.batch_scale)
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"] = run_adjoint_figure(prs, stream, dev)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.interval)
     if rank == 0:
@@ -347,6 +355,100 @@ def run_e2e(args, prs, sim, shape, stream, dev, world) -> dict:
     return {"value": sites * args.interval * k * world / secs, "unit": "site-updates/s",
             "h2d_bytes_per_step": 2 * sites * 4, "d2h_bytes_per_step": 48, "steps": k,
             "path": "prs_set_state(host) + prs_step + prs_measure"}
+
+
+def ensemble_runs(scale: float = 1.0):
+    """The ensemble of independent runs: 16 each of 2D 256^2, 1024^2, 2048^2 and 3D 128^3, FP32,
+    seeds 1000+i, expansion exponent m drawn from {1, 2} by a host RNG seeded with 42, each run to
+    eta = N/2 (deta = 0.1, eta0 = 1: 10 N/2 - 10 steps)."""
+    rng = np.random.Generator(np.random.PCG64(42))
+    runs = []
+    i = 0
+    for shape in [(256, 256)] * 16 + [(1024, 1024)] * 16 + [(2048, 2048)] * 16 + [(128, 128, 128)] * 16:
+        m = float(rng.integers(1, 3))
+        n = shape[0]
+        nsteps = int(round(((n / 2) - 1.0) / 0.1))
+        runs.append((shape, m, 1000 + i, max(1, int(nsteps * scale))))
+        i += 1
+    return runs
+
+
+def run_batch_figure(prs, stream, dev, scale: float) -> dict:
+    """Batched persistent launch vs one prs_step loop per run, on the same ensemble and outputs."""
+    import torch
+
+    runs = ensemble_runs(scale)
+    every = 20
+    total = sum(int(np.prod(s)) * n for s, _, _, n in runs)
+    params = [prs.make_params(s, era_m=m, seed=sd) for s, m, sd, _ in runs]
+    t0 = time.perf_counter()
+    b = prs.prs_batch_create(params, stream.cuda_stream)
+    t_create = time.perf_counter() - t0
+    cap = max(n for *_, n in runs) // every + 1
+    ns = [n for *_, n in runs]
+    torch.cuda.synchronize(dev)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    out = prs.prs_batch_run(b, ns, measure_every=every, out_capacity=cap)
+    z.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_batch = a.elapsed_time(z)
+    tl = {f"{s[0]}^{len(s)}": prs.prs_batch_tuning(b, k)[0] for k, (s, *_r) in enumerate(runs)}
+    budget = prs.prs_batch_tuning(b, 0)[1]
+    prs.prs_batch_destroy(b)
+    # one run at a time: prs_step between outputs, prs_measure at each output
+    a.record(stream)
+    for (s, m, sd, n) in runs:
+        sim = prs.Sim(s, stream=stream, device=dev, era_m=m, seed=sd)
+        sim.init()
+        done = 0
+        prs.prs_measure_ex(sim.handle)
+        while done < n:
+            k = min(every, n - done)
+            prs.prs_step(sim.handle, k)
+            done += k
+            if done % every == 0:
+                prs.prs_measure_ex(sim.handle)
+        sim.close()
+    z.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_seq = a.elapsed_time(z)
+    return {"workload": "16 x 2D 256^2, 16 x 1024^2, 16 x 2048^2 and 16 x 3D 128^3, FP32, each to eta = N/2"
+                        + ("" if scale == 1.0 else f" x {scale} of the steps") + ", diagnostics every 20 steps",
+            "site_updates": total, "batched_s": ms_batch / 1e3, "one_at_a_time_s": ms_seq / 1e3,
+            "batched_value": total / (ms_batch / 1e3), "one_at_a_time_value": total / (ms_seq / 1e3),
+            "unit": "site-updates/s", "speedup": ms_seq / ms_batch, "create_s": t_create,
+            "tuned_tile_len": tl, "tuned_group_bytes": budget, "first_output_run0": list(out[0, 0])}
+
+
+def run_adjoint_figure(prs, stream, dev) -> dict:
+    """3D 256^3 FP32: forward to eta = 128 (1270 steps) vs prs_adjoint with checkpoints every 64 steps."""
+    import torch
+
+    shape, nsteps, K = (256, 256, 256), 1270, 64
+    sim = prs.Sim(shape, stream=stream, device=dev, seed=5)
+    sim.init()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    prs.prs_step(sim.handle, nsteps)
+    z.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_fwd = a.elapsed_time(z)
+    sim.close()
+    sim = prs.Sim(shape, stream=stream, device=dev, seed=5)
+    sim.init()
+    g = torch.empty(tuple(reversed(shape)), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    J, dA = prs.prs_adjoint(sim.handle, nsteps, prs.PRS_OBS_SMOOTH_AREA, 0.1, K, g, None)
+    torch.cuda.synchronize(dev)
+    s_adj = time.perf_counter() - t0
+    sim.close()
+    return {"workload": "3D 256^3 FP32, eta 1 -> 128 (1270 steps), checkpoints every 64 steps, "
+                        "J = tanh(phi/0.1)-smoothed wall area", "forward_s": ms_fwd / 1e3, "adjoint_s": s_adj,
+            "adjoint_over_forward": s_adj / (ms_fwd / 1e3),
+            "note": "adjoint_s covers the forward pass with checkpoints, the segment recomputation and the "
+                    "reverse sweep", "J": J, "dJ_dalpha": dA}
 
 
 def main():
