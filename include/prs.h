@@ -216,10 +216,13 @@ int prs_observable(prs_sim* sim, int observable, double eps_smooth, double* J);
  *   *J, *dJ_dalpha (host, FP64);
  *   d_dJ_dphi_init, d_dJ_dv_init: caller-owned device arrays of the run's layout and
  *   precision (either may be NULL), receiving dJ/dphi and dJ/d(dphi) at the start.
- * Memory: a checkpoint of (phi, dphi) every ckpt_every steps plus ckpt_every-1
- * states of one segment, allocated for the call and freed before it returns.
- * Reverse sweep per segment: recompute its states from the checkpoint, then apply
- *   lt = lv' + deta lphi',  lphi = lphi' + c2 (L lt - f'(phi) lt),  lv = c1 lt,
+ * Memory: with ckpt_every = K > 0, a checkpoint of (phi, dphi) every K steps plus
+ * K-1 states of one segment, each segment recomputed from its checkpoint before it
+ * is swept backwards; with ckpt_every = 0, every state when nsteps+1 states fit in
+ * free device memory (no recomputation), else K = 64.  This working memory stays
+ * with the run for the next call (grown when a call needs more) and is released by
+ * prs_destroy.  Reverse step n, with lt = lv' + deta lphi':
+ *   lphi = lphi' + c2 (L lt - f'(phi) lt),  lv = c1 lt,
  *   dJ/dalpha += sum lt (dc1/dalpha dphi + dc2/dalpha (L phi - f(phi))).
  * On return the run holds the state at step n+nsteps.  Synchronises. */
 int prs_adjoint(prs_sim* sim, int64_t nsteps, int observable, double eps_smooth, int64_t ckpt_every, double* J,

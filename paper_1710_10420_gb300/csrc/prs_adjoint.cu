@@ -13,10 +13,19 @@
 // with d delta/d alpha = deta m/(2 eta_n), dc1/d delta = -2/(1+delta)^2,
 // dc2/d delta = -deta/(1+delta)^2.
 //
-// The forward states come from checkpoints every K steps; each segment is
-// recomputed into segment storage (the step kernel writes phi and dphi out of
-// place), then walked backwards.  The state is never inverted algebraically:
-// 1/c1 grows without bound as delta -> 1.
+// The sweep carries lphi (pointwise) and lt (the only adjoint field read across
+// sites): step n reads lt_n with its neighbours, phi^n with its neighbours (for
+// L phi in dJ/dalpha), and dphi^n, lphi_{n+1} pointwise, and writes
+//     lphi_n = lphi_{n+1} + c2 (L lt_n - f'(phi^n) lt_n),  lt_{n-1} = c1 lt_n + deta lphi_n
+// (at the first step of the run it writes lv_n0 = c1 lt_n0 instead): 24 bytes per
+// site in FP32, one pass.  The FP32 kernels stage phi^n and lt_n in shared memory
+// like the forward step (prs_tile.cuh).
+//
+// The forward states are either all kept (when they fit in device memory: GB300's
+// HBM holds e.g. 1271 states of a 256^3 FP32 run) or checkpointed every K steps
+// and each segment recomputed into segment storage (the step kernel writes phi
+// and dphi out of place) before it is walked backwards.  The state is never
+// inverted algebraically: 1/c1 grows without bound as delta -> 1.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -29,6 +38,7 @@
 #include "prs_internal.h"
 #include "prs_reduce.cuh"
 #include "prs_sim.h"
+#include "prs_tile.cuh"
 
 namespace prs {
 
@@ -76,8 +86,9 @@ struct AdjCoef {
 
 // J contribution of the links (s, s+e_d) and dJ/dphi_s (written to grad).
 template <typename R, int D>
-__global__ void __launch_bounds__(256) k_observable(const R* __restrict__ phi, R* __restrict__ grad, Geo g, int obs,
-                                                    double eps, double inv_dx2, double area_scale, DiagScratch scr)
+__global__ void __launch_bounds__(256) k_observable(const R* __restrict__ phi, R* __restrict__ grad,
+                                                    R* __restrict__ grad_deta, Geo g, int obs, double eps,
+                                                    double inv_dx2, double area_scale, double deta, DiagScratch scr)
 {
     double J = 0.0;
     PRS_FOR_SITES(g, s, x, y, z)
@@ -103,17 +114,19 @@ __global__ void __launch_bounds__(256) k_observable(const R* __restrict__ phi, R
             gr = -0.5 * area_scale * (1.0 - ss * ss) / eps * nb;
         }
         grad[s] = (R)gr;
+        if (grad_deta) grad_deta[s] = (R)gr * (R)deta;  // lt at the last step: lv = 0 there
     }
     block_reduce_and_finish(DiagAcc{J, 0.0, 0, 0, 0, 0}, scr);
 }
 
-// One reverse step: (lphi_in, lv_in) at n+1 -> (lphi_out, lv_out) at n, using the
-// forward state (phi, v) at n; the dJ/dalpha term of this step lands in *scr.result.
+// One reverse step n: lt_in = lt_n, lphi = lphi_{n+1} (updated in place to lphi_n),
+// lt_out = lt_{n-1} (or lv_n at the run's first step, `last`), using the forward
+// state (phi, v) at n; the dJ/dalpha term of this step lands in *scr.result.
 template <typename R, int D>
 __global__ void __launch_bounds__(256)
-    k_adjoint_step(const R* __restrict__ phi, const R* __restrict__ v, const R* __restrict__ lphi_in,
-                   const R* __restrict__ lv_in, R* __restrict__ lphi_out, R* __restrict__ lv_out, Geo g, AdjCoef c,
-                   RunConst<R> rc, DiagScratch scr)
+    k_adjoint_step(const R* __restrict__ phi, const R* __restrict__ v, const R* __restrict__ lt_in,
+                   R* __restrict__ lphi, R* __restrict__ lt_out, Geo g, AdjCoef c, RunConst<R> rc, bool last,
+                   DiagScratch scr)
 {
     const R c1 = (R)c.c1, c2 = (R)c.c2, cV = (R)c.cV, deta = rc.deta;
     const R dc1 = (R)c.dc1, dc2 = (R)c.dc2;
@@ -123,16 +136,13 @@ __global__ void __launch_bounds__(256)
     PRS_FOR_SITES(g, s, x, y, z)
     {
         const Nbr n = neighbours(g, s, x, y, z);
-        auto lt = [&](int64_t q) { return lv_in[q] + deta * lphi_in[q]; };
-        const R lts = lt(s);
-        R s2 = lt(n.xp) + lt(n.xm);
-        s2 = s2 + (lt(n.yp) + lt(n.ym));
-        if (D == 3) s2 = s2 + (lt(n.zp) + lt(n.zm));
-        const R Llt = (s2 - rc.twoD * lts) * rc.inv_dx2;
+        const R lts = lt_in[s];
+        const R Llt = (pair_sum<R, D>(lt_in, n) - rc.twoD * lts) * rc.inv_dx2;
         const R p = phi[s];
         const R fprime = cV * ((R)3 * (p * p) * rc.inv_phi0sq - (R)1);
-        lphi_out[s] = lphi_in[s] + c2 * (Llt - fprime * lts);
-        lv_out[s] = c1 * lts;
+        const R lp = lphi[s] + c2 * (Llt - fprime * lts);
+        lphi[s] = lp;
+        lt_out[s] = last ? c1 * lts : c1 * lts + deta * lp;
         const R Lphi = (pair_sum<R, D>(phi, n) - rc.twoD * p) * rc.inv_dx2;
         const R f = (cV * p) * ((p * p) * rc.inv_phi0sq - (R)1);
         const R term = lts * (dc1 * v[s] + dc2 * (Lphi - f));
@@ -142,6 +152,318 @@ __global__ void __launch_bounds__(256)
         da = t;
     }
     block_reduce_and_finish(DiagAcc{(double)da, 0.0, 0, 0, 0, 0}, scr);
+}
+
+// ------------------------------------------------------- staged FP32 sweep
+
+constexpr int kAdjItems = 2;  // float4 per thread per plane: 2048 sites per plane tile
+
+struct AdjTile {
+    const float* phi;    // phi^n (stencil)
+    const float* lt_in;  // lt_n (stencil)
+    const float* v;      // dphi^n (pointwise)
+    float* lphi;         // lphi_{n+1} -> lphi_n (pointwise, in place)
+    float* lt_out;       // lt_{n-1}, or lv_n when last
+    int nx, ny, nz, t;   // box; t = rows per plane tile (3D) or per band (2D)
+    int y0, z0, len;     // first row, first plane (3D), planes (3D) or rows (2D)
+};
+
+struct AdjCoefF {
+    float c1, c2, cV, dc1, dc2;
+};
+
+// 4 pair sums (x+ + x-) + (y+ + y-) [+ (z+ + z-)] of a float4 and its neighbours.
+__device__ __forceinline__ float4 pairs4(float4 c, float left, float right, float4 yp, float4 ym, float4 zp, float4 zm,
+                                         bool three_d)
+{
+    float4 r;
+    r.x = (c.y + left) + (yp.x + ym.x);
+    r.y = (c.z + c.x) + (yp.y + ym.y);
+    r.z = (c.w + c.y) + (yp.z + ym.z);
+    r.w = (right + c.z) + (yp.w + ym.w);
+    if (three_d) {
+        r.x = r.x + (zp.x + zm.x);
+        r.y = r.y + (zp.y + zm.y);
+        r.z = r.z + (zp.z + zm.z);
+        r.w = r.w + (zp.w + zm.w);
+    }
+    return r;
+}
+
+struct AdjSum {  // per-thread compensated FP32 sum, folded into FP64 once per plane
+    double tot;
+    float s, comp;
+    __device__ __forceinline__ void add(float term)
+    {
+        const float yk = term - comp;
+        const float t = s + yk;
+        comp = (t - s) - yk;
+        s = t;
+    }
+    __device__ __forceinline__ void fold()
+    {
+        tot += (double)s;
+        s = 0.0f;
+        comp = 0.0f;
+    }
+};
+
+// The pointwise part of one reverse step for 4 sites.
+__device__ __forceinline__ void adj_update4(float4 p, float4 sp, float4 l, float4 sl, float4 vv, float4& lp, float4& out,
+                                            const AdjCoefF& k, const RunConst<float>& rc, bool last, AdjSum& da)
+{
+    const float pc[4] = {p.x, p.y, p.z, p.w}, spc[4] = {sp.x, sp.y, sp.z, sp.w};
+    const float lc[4] = {l.x, l.y, l.z, l.w}, slc[4] = {sl.x, sl.y, sl.z, sl.w};
+    const float vc[4] = {vv.x, vv.y, vv.z, vv.w};
+    float lpo[4] = {lp.x, lp.y, lp.z, lp.w}, o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float q = pc[e], lt = lc[e];
+        const float Llt = (slc[e] - rc.twoD * lt) * rc.inv_dx2;
+        const float fprime = k.cV * (3.0f * (q * q) * rc.inv_phi0sq - 1.0f);
+        const float lpn = lpo[e] + k.c2 * (Llt - fprime * lt);
+        lpo[e] = lpn;
+        o[e] = last ? k.c1 * lt : k.c1 * lt + rc.deta * lpn;
+        const float Lphi = (spc[e] - rc.twoD * q) * rc.inv_dx2;
+        const float f = (k.cV * q) * ((q * q) * rc.inv_phi0sq - 1.0f);
+        da.add(lt * (k.dc1 * vc[e] + k.dc2 * (Lphi - f)));
+    }
+    lp = make_float4(lpo[0], lpo[1], lpo[2], lpo[3]);
+    out = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+// 3D: a tile of t rows x len planes; phi^n and lt_n staged plane by plane in two
+// 4-slot rings (one mbarrier per slot counts both copies).
+template <int ITEMS>
+__global__ void __launch_bounds__(kFastThreads, 2)
+    k_adjoint3d_f32(AdjTile T, AdjCoefF k, RunConst<float> rc, bool last, DiagScratch scr, unsigned int* err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    const int nx = T.nx, ny = T.ny, nz = T.nz, ty = T.t;
+    const int tile = (ty + 2) * nx;
+    float* ringP = reinterpret_cast<float*>(smem_raw + 128);
+    float* ringL = ringP + 4 * tile;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int ytiles = ny / ty;
+    const int y0 = (blockIdx.x % ytiles) * ty;
+    const int z0 = (blockIdx.x / ytiles) * T.len;
+    const int zn = min(T.len, nz - z0);
+    const int nq = nx >> 2;
+    const size_t plane = (size_t)nx * ny;
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int ytop = (y0 == 0 ? ny : y0) - 1;
+    const int ybot = (y0 + ty == ny) ? 0 : y0 + ty;
+    const unsigned rowb = (unsigned)nx * 4u;
+    const int nloc = zn + 2;
+    auto issue = [&](int i) {
+        int p = z0 - 1 + i;
+        p = p < 0 ? p + nz : (p >= nz ? p - nz : p);
+        uint64_t* b = &bar[i & 3];
+        mbar_arrive_expect_tx(b, 2u * rowb * (unsigned)(ty + 2));
+        const float* srcs[2] = {T.phi + (size_t)p * plane, T.lt_in + (size_t)p * plane};
+        float* dsts[2] = {ringP + (i & 3) * tile, ringL + (i & 3) * tile};
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            bulk_g2s(dsts[f], srcs[f] + (size_t)ytop * nx, rowb, b);
+            bulk_g2s(dsts[f] + nx, srcs[f] + (size_t)y0 * nx, rowb * (unsigned)ty, b);
+            bulk_g2s(dsts[f] + (size_t)(ty + 1) * nx, srcs[f] + (size_t)ybot * nx, rowb, b);
+        }
+    };
+    int issued = -1;
+    if (tid == 0)
+        for (int i = 0; i < 3 && i < nloc; ++i) issue(i), issued = i;
+    int row[ITEMS], col[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        int q = tid + kFastThreads * j;
+        row[j] = q / nq;
+        col[j] = q - row[j] * nq;
+    }
+    float4 vc[ITEMS], lc[ITEMS];
+    {
+        const size_t b0 = (size_t)z0 * plane + (size_t)y0 * nx;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            vc[j] = ldg_stream4(T.v + b0 + (size_t)row[j] * nx + 4 * col[j]);
+            lc[j] = ldg_stream4(T.lphi + b0 + (size_t)row[j] * nx + 4 * col[j]);
+        }
+    }
+    AdjSum da{0.0, 0.0f, 0.0f};
+    for (int zi = 0; zi < zn; ++zi) {
+        bool ok = true;
+        if (zi == 0) ok = mbar_wait(&bar[0], 0, err) && mbar_wait(&bar[1], 0, err);
+        ok = ok && mbar_wait(&bar[(zi + 2) & 3], ((zi + 2) >> 2) & 1, err);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) drain(bar, zi, issued, err);
+            break;
+        }
+        if (tid == 0 && zi + 3 < nloc) issue(zi + 3), issued = zi + 3;
+        const int z = z0 + zi;
+        float4 vn[ITEMS], ln[ITEMS];
+        if (zi + 1 < zn) {
+            const size_t b1 = (size_t)(z + 1) * plane + (size_t)y0 * nx;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                vn[j] = ldg_stream4(T.v + b1 + (size_t)row[j] * nx + 4 * col[j]);
+                ln[j] = ldg_stream4(T.lphi + b1 + (size_t)row[j] * nx + 4 * col[j]);
+            }
+        }
+        const int sm = (zi & 3) * tile + nx, sc = ((zi + 1) & 3) * tile + nx, sp = ((zi + 2) & 3) * tile + nx;
+        const size_t bz = (size_t)z * plane + (size_t)y0 * nx;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int off = row[j] * nx + 4 * col[j];
+            float4 P[2], S[2];
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const float* R = f == 0 ? ringP : ringL;
+                const float4 c = lds4(R + sc + off);
+                float left, right;
+                x_halo(R + sc + row[j] * nx, col[j], nq, nx, lane, c, left, right);
+                P[f] = c;
+                S[f] = pairs4(c, left, right, lds4(R + sc + off + nx), lds4(R + sc + off - nx), lds4(R + sp + off),
+                              lds4(R + sm + off), true);
+            }
+            float4 out;
+            adj_update4(P[0], S[0], P[1], S[1], vc[j], lc[j], out, k, rc, last, da);
+            stg4(T.lphi + bz + off, lc[j]);
+            stg4(T.lt_out + bz + off, out);
+        }
+        da.fold();
+        if (zi + 1 < zn) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j], lc[j] = ln[j];
+        }
+    }
+    block_reduce_and_finish(DiagAcc{da.tot, 0.0, 0, 0, 0, 0}, scr);
+}
+
+// 2D: a tile of len rows in bands of t rows; band 0 = the row above, nb+1 = below.
+template <int ITEMS>
+__global__ void __launch_bounds__(kFastThreads, 2)
+    k_adjoint2d_f32(AdjTile T, AdjCoefF k, RunConst<float> rc, bool last, DiagScratch scr, unsigned int* err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    const int nx = T.nx, ny = T.ny, rb = T.t;
+    const int slot = rb * nx;
+    float* ringP = reinterpret_cast<float*>(smem_raw + 128);
+    float* ringL = ringP + 4 * slot;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int y0 = blockIdx.x * T.len;
+    const int yn = min(T.len, ny - y0);
+    const int nb = yn / rb;
+    const int nq = nx >> 2;
+    const int ringrows = 4 * rb;
+    const unsigned rowb = (unsigned)nx * 4u;
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int nloc = nb + 2;
+    auto issue = [&](int i) {
+        uint64_t* b = &bar[i & 3];
+        const float* srcs[2] = {T.phi, T.lt_in};
+        float* dsts[2] = {ringP + (i & 3) * slot, ringL + (i & 3) * slot};
+        if (i == 0 || i == nb + 1) {
+            const int y = i == 0 ? (y0 == 0 ? ny : y0) - 1 : ((y0 + yn == ny) ? 0 : y0 + yn);
+            const int r = i == 0 ? rb - 1 : 0;
+            mbar_arrive_expect_tx(b, 2u * rowb);
+#pragma unroll
+            for (int f = 0; f < 2; ++f) bulk_g2s(dsts[f] + (size_t)r * nx, srcs[f] + (size_t)y * nx, rowb, b);
+        } else {
+            const int y = y0 + (i - 1) * rb;
+            mbar_arrive_expect_tx(b, 2u * rowb * (unsigned)rb);
+#pragma unroll
+            for (int f = 0; f < 2; ++f) bulk_g2s(dsts[f], srcs[f] + (size_t)y * nx, rowb * (unsigned)rb, b);
+        }
+    };
+    int issued = -1;
+    if (tid == 0)
+        for (int i = 0; i < 3 && i < nloc; ++i) issue(i), issued = i;
+    int row[ITEMS], col[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        int q = tid + kFastThreads * j;
+        row[j] = q / nq;
+        col[j] = q - row[j] * nq;
+    }
+    float4 vc[ITEMS], lc[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const size_t o = (size_t)(y0 + row[j]) * nx + 4 * col[j];
+        vc[j] = ldg_stream4(T.v + o);
+        lc[j] = ldg_stream4(T.lphi + o);
+    }
+    AdjSum da{0.0, 0.0f, 0.0f};
+    for (int bi = 0; bi < nb; ++bi) {
+        bool ok = true;
+        if (bi == 0) ok = mbar_wait(&bar[0], 0, err) && mbar_wait(&bar[1], 0, err);
+        ok = ok && mbar_wait(&bar[(bi + 2) & 3], ((bi + 2) >> 2) & 1, err);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) drain(bar, bi, issued, err);
+            break;
+        }
+        if (tid == 0 && bi + 3 < nloc) issue(bi + 3), issued = bi + 3;
+        const int yb = y0 + bi * rb;
+        float4 vn[ITEMS], ln[ITEMS];
+        if (bi + 1 < nb) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const size_t o = (size_t)(yb + rb + row[j]) * nx + 4 * col[j];
+                vn[j] = ldg_stream4(T.v + o);
+                ln[j] = ldg_stream4(T.lphi + o);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int lr = (bi + 1) * rb + row[j];
+            const int rc0 = (lr % ringrows) * nx, ru = ((lr + ringrows - 1) % ringrows) * nx,
+                      rd = ((lr + 1) % ringrows) * nx;
+            float4 P[2], S[2];
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const float* R = f == 0 ? ringP : ringL;
+                const float4 c = lds4(R + rc0 + 4 * col[j]);
+                float left, right;
+                x_halo(R + rc0, col[j], nq, nx, lane, c, left, right);
+                P[f] = c;
+                const float4 ym = lds4(R + ru + 4 * col[j]), yp = lds4(R + rd + 4 * col[j]);
+                S[f] = pairs4(c, left, right, yp, ym, ym, ym, false);
+            }
+            float4 out;
+            adj_update4(P[0], S[0], P[1], S[1], vc[j], lc[j], out, k, rc, last, da);
+            const size_t o = (size_t)(yb + row[j]) * nx + 4 * col[j];
+            stg4(T.lphi + o, lc[j]);
+            stg4(T.lt_out + o, out);
+        }
+        da.fold();
+        if (bi + 1 < nb) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j], lc[j] = ln[j];
+        }
+    }
+    block_reduce_and_finish(DiagAcc{da.tot, 0.0, 0, 0, 0, 0}, scr);
+}
+
+// FP32 boxes the staged sweep takes: x a multiple of 128 dividing 2048 (2D and 3D),
+// y divisible by the rows of a tile, and the two rings within 113 KB.
+bool adj_fast_ok(const Geo& g, int precision)
+{
+    if (precision != PRS_FP32) return false;
+    if (g.nx % 128 != 0 || g.nx > kAdjItems * 1024 || (kAdjItems * 1024) % g.nx != 0) return false;
+    const int t = kAdjItems * 1024 / g.nx;
+    if (g.ny % t != 0) return false;
+    const size_t sm = g.dims == 3 ? 128 + 2 * 4 * (size_t)(t + 2) * g.nx * 4 : 128 + 2 * 4 * (size_t)t * g.nx * 4;
+    return sm <= 113 * 1024;
 }
 
 // Grid of the row-wise kernels: x blocks cover a row, y blocks stride over rows;
@@ -161,14 +483,15 @@ RunConst<R> run_const(const double* rcd)
     return RunConst<R>{(R)rcd[0], (R)rcd[1], (R)rcd[2], (R)rcd[3], (R)rcd[4], (R)rcd[5]};
 }
 
-cudaError_t launch_observable(const prs_sim* s, const void* phi, void* grad, int obs, double eps, DiagScratch scr)
+cudaError_t launch_observable(const prs_sim* s, const void* phi, void* grad, void* grad_deta, int obs, double eps,
+                              DiagScratch scr)
 {
     const double area_scale = 1.0 / ((double)s->g.S * s->p.dx);
     const dim3 grid = grid_for(s->g);
     if ((int)(grid.x * grid.y) > scr.max_blocks) return cudaErrorInvalidValue;
 #define PRS_OBS_LAUNCH(R, D)                                                                                     \
-    k_observable<R, D><<<grid, 256, 0, s->stream>>>((const R*)phi, (R*)grad, s->g, obs, eps, s->rc[1], area_scale, \
-                                                    scr)
+    k_observable<R, D><<<grid, 256, 0, s->stream>>>((const R*)phi, (R*)grad, (R*)grad_deta, s->g, obs, eps,       \
+                                                    s->rc[1], area_scale, s->p.deta, scr)
     if (s->p.precision == PRS_FP32) {
         if (s->g.dims == 3) PRS_OBS_LAUNCH(float, 3); else PRS_OBS_LAUNCH(float, 2);
     } else {
@@ -178,18 +501,83 @@ cudaError_t launch_observable(const prs_sim* s, const void* phi, void* grad, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_step(const prs_sim* s, const void* phi, const void* v, const void* lphi_in,
-                                const void* lv_in, void* lphi_out, void* lv_out, const AdjCoef& c, DiagScratch scr)
+int adj_sm_count()
 {
-    const dim3 grid = grid_for(s->g);
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+cudaError_t launch_adjoint_step(const prs_sim* s, const void* phi, const void* v, const void* lt_in, void* lphi,
+                                void* lt_out, const AdjCoef& c, bool last, DiagScratch scr, unsigned int* err)
+{
+    const Geo& g = s->g;
+    if (adj_fast_ok(g, s->p.precision)) {
+        static bool attr3 = false, attr2 = false;
+        const int t = kAdjItems * 1024 / g.nx;
+        const int slots = 2 * adj_sm_count();
+        AdjTile T{(const float*)phi, (const float*)lt_in, (const float*)v, (float*)lphi, (float*)lt_out,
+                  g.nx, g.ny, g.nz, t, 0, 0, 0};
+        AdjCoefF k{(float)c.c1, (float)c.c2, (float)c.cV, (float)c.dc1, (float)c.dc2};
+        RunConst<float> rc = run_const<float>(s->rc);
+        if (g.dims == 3) {
+            const size_t sm = 128 + 2 * 4 * (size_t)(t + 2) * g.nx * 4;
+            if (!attr3) {
+                cudaError_t e = cudaFuncSetAttribute(k_adjoint3d_f32<kAdjItems>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+                if (e != cudaSuccess) return e;
+                attr3 = true;
+            }
+            const int ytiles = g.ny / t;
+            // z-chunks: whole waves of resident CTAs, chunks of >= 8 planes, one partial per block
+            int best = 1;
+            double best_score = -1;
+            for (int nc = 1; nc <= g.nz / 8 || nc == 1; ++nc) {
+                const int cz = (g.nz + nc - 1) / nc, n = (g.nz + cz - 1) / cz;
+                const long long blocks = (long long)ytiles * n;
+                if (blocks > scr.max_blocks) break;
+                const long long waves = (blocks + slots - 1) / slots;
+                const double score = (double)blocks / (double)(waves * slots) * cz / (cz + 2.0);
+                if (score > best_score + 1e-9) best_score = score, best = n;
+            }
+            T.len = (g.nz + best - 1) / best;
+            const int blocks = ytiles * ((g.nz + T.len - 1) / T.len);
+            k_adjoint3d_f32<kAdjItems><<<blocks, kFastThreads, sm, s->stream>>>(T, k, rc, last, scr, err);
+            return cudaGetLastError();
+        }
+        const size_t sm = 128 + 2 * 4 * (size_t)t * g.nx * 4;
+        if (!attr2) {
+            cudaError_t e = cudaFuncSetAttribute(k_adjoint2d_f32<kAdjItems>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+            if (e != cudaSuccess) return e;
+            attr2 = true;
+        }
+        const int bands = g.ny / t;
+        int nb = (bands + 4 * slots - 1) / (4 * slots);  // bands per tile: about four waves of tiles
+        if (nb < 4) nb = 4;
+        T.len = nb * t;
+        int blocks = (g.ny + T.len - 1) / T.len;
+        if (blocks > scr.max_blocks) {
+            T.len = ((g.ny + scr.max_blocks - 1) / scr.max_blocks + t - 1) / t * t;
+            blocks = (g.ny + T.len - 1) / T.len;
+        }
+        k_adjoint2d_f32<kAdjItems><<<blocks, kFastThreads, sm, s->stream>>>(T, k, rc, last, scr, err);
+        return cudaGetLastError();
+    }
+    const dim3 grid = grid_for(g);
     if ((int)(grid.x * grid.y) > scr.max_blocks) return cudaErrorInvalidValue;
-#define PRS_ADJ_LAUNCH(R, D)                                                                                         \
-    k_adjoint_step<R, D><<<grid, 256, 0, s->stream>>>((const R*)phi, (const R*)v, (const R*)lphi_in, (const R*)lv_in, \
-                                                      (R*)lphi_out, (R*)lv_out, s->g, c, run_const<R>(s->rc), scr)
+#define PRS_ADJ_LAUNCH(R, D)                                                                                  \
+    k_adjoint_step<R, D><<<grid, 256, 0, s->stream>>>((const R*)phi, (const R*)v, (const R*)lt_in, (R*)lphi, \
+                                                      (R*)lt_out, g, c, run_const<R>(s->rc), last, scr)
     if (s->p.precision == PRS_FP32) {
-        if (s->g.dims == 3) PRS_ADJ_LAUNCH(float, 3); else PRS_ADJ_LAUNCH(float, 2);
+        if (g.dims == 3) PRS_ADJ_LAUNCH(float, 3); else PRS_ADJ_LAUNCH(float, 2);
     } else {
-        if (s->g.dims == 3) PRS_ADJ_LAUNCH(double, 3); else PRS_ADJ_LAUNCH(double, 2);
+        if (g.dims == 3) PRS_ADJ_LAUNCH(double, 3); else PRS_ADJ_LAUNCH(double, 2);
     }
 #undef PRS_ADJ_LAUNCH
     return cudaGetLastError();
@@ -230,7 +618,7 @@ extern "C" int prs_observable(prs_sim* s, int observable, double eps_smooth, dou
     void* grad = mem.get((size_t)s->g.S * s->elem);
     if (!grad) return PRS_ENOMEM;
     DiagScratch scr = s->scr;
-    cudaError_t e = launch_observable(s, s->phi[s->cur], grad, observable, eps_smooth, scr);
+    cudaError_t e = launch_observable(s, s->phi[s->cur], grad, nullptr, observable, eps_smooth, scr);
     if (e != cudaSuccess) return cuda_fail(e, "prs_observable launch");
     e = cudaMemcpyAsync(s->h_status, s->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -242,32 +630,56 @@ extern "C" int prs_observable(prs_sim* s, int observable, double eps_smooth, dou
 extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double eps_smooth, int64_t ckpt_every,
                            double* J, double* dJ_dalpha, void* d_dJ_dphi_init, void* d_dJ_dv_init)
 {
-    if (!s || nsteps < 0 || ckpt_every < 1) return PRS_EINVAL;
+    if (!s || nsteps < 0 || ckpt_every < 0) return PRS_EINVAL;
     if (observable != PRS_OBS_GRAD_ENERGY && observable != PRS_OBS_SMOOTH_AREA) return PRS_EINVAL;
     if (observable == PRS_OBS_SMOOTH_AREA && !(eps_smooth > 0)) return PRS_EINVAL;
     if (!s->initialised) return PRS_ESTATE;
     if (nsteps > 0 && !cfl_ok(s->p, s->n + nsteps - 1)) return PRS_EINVAL;
     const size_t fbytes = (size_t)s->g.S * s->elem;
     const int64_t n0 = s->n;
-    const int64_t K = ckpt_every < nsteps ? ckpt_every : (nsteps > 0 ? nsteps : 1);
-    const int64_t nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
     const bool repro = (s->p.flags & PRS_REPRO) != 0;
+    // every state kept (K = nsteps, no recomputation) when asked with ckpt_every = 0
+    // and it fits in device memory with 2 GB to spare; else checkpoints every K
+    int64_t K = ckpt_every;
+    bool keep_all = false;
+    if (ckpt_every == 0) {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const double need = 2.0 * (double)fbytes * (double)(nsteps + 1) + 3.0 * (double)fbytes + 2e9;
+        keep_all = need <= (double)free_b + (double)s->adj_ws_bytes;  // the kept workspace is reusable
+        K = keep_all ? (nsteps > 0 ? nsteps : 1) : 64;
+    }
+    if (K > nsteps) K = nsteps > 0 ? nsteps : 1;
+    const int64_t nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
 
-    Scratch mem;
-    char* ckpt = nseg ? (char*)mem.get(2 * fbytes * (size_t)nseg) : nullptr;  // (phi, v) at n0 + i K
-    char* seg = K > 1 ? (char*)mem.get(2 * fbytes * (size_t)(K - 1)) : nullptr;  // states 1..K-1 of a segment
-    char* adj = (char*)mem.get(4 * fbytes);                                        // lphi[2], lv[2]
-    DiagAcc* dacc = (DiagAcc*)mem.get(sizeof(DiagAcc) * (size_t)(nsteps > 0 ? nsteps : 1));
-    if ((nseg && !ckpt) || (K > 1 && !seg) || !adj || !dacc) return PRS_ENOMEM;
+    // one workspace, kept with the run for the next call: [states][lphi, lt[2]][dacc].
+    // keep_all: states 0..nsteps back to back; else one checkpoint per segment plus
+    // states 1..K-1 of the segment being swept
+    const size_t nstate = keep_all ? (size_t)(nsteps + 1) : (size_t)nseg + (size_t)(K > 1 ? K - 1 : 0);
+    const size_t need = 2 * fbytes * nstate + 3 * fbytes + sizeof(DiagAcc) * (size_t)(nsteps > 0 ? nsteps : 1);
+    if (s->adj_ws_bytes < need) {
+        cudaFree(s->adj_ws);
+        s->adj_ws = nullptr;
+        s->adj_ws_bytes = 0;
+        if (cudaMalloc(&s->adj_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            s->adj_ws = nullptr;
+            return PRS_ENOMEM;
+        }
+        s->adj_ws_bytes = need;
+    }
+    char* ckpt = (char*)s->adj_ws;
+    char* seg = keep_all ? nullptr : ckpt + 2 * fbytes * (size_t)nseg;
+    char* adj = ckpt + 2 * fbytes * nstate;  // lphi, lt[2]
+    DiagAcc* dacc = (DiagAcc*)(adj + 3 * fbytes);
     std::vector<DiagAcc> hacc((size_t)(nsteps > 0 ? nsteps : 1));
 
-    auto cphi = [&](int64_t i) { return ckpt + 2 * fbytes * (size_t)i; };
-    auto sphi = [&](int64_t k, int64_t i) -> char* {  // state k (0..K-1) of segment i
-        return k == 0 ? cphi(i) : seg + 2 * fbytes * (size_t)(k - 1);
+    auto state = [&](int64_t k, int64_t i) -> char* {  // state k (0..K-1) of segment i
+        if (keep_all) return ckpt + 2 * fbytes * (size_t)(i * K + k);
+        return k == 0 ? ckpt + 2 * fbytes * (size_t)i : seg + 2 * fbytes * (size_t)(k - 1);
     };
-    auto sv = [&](int64_t k, int64_t i) -> char* { return sphi(k, i) + fbytes; };
-    char* lphi[2] = {adj, adj + fbytes};
-    char* lv[2] = {adj + 2 * fbytes, adj + 3 * fbytes};
+    char* lphi = adj;
+    char* lt[2] = {adj + fbytes, adj + 2 * fbytes};
     unsigned int* err = &s->d_status->error;
     cudaStream_t st = s->stream;
 #define PRS_TRY(call)                                              \
@@ -276,29 +688,48 @@ extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double ep
         if (e_ != cudaSuccess) return cuda_fail(e_, "prs_adjoint"); \
     } while (0)
 
-    // forward, keeping a checkpoint at the start of every segment
-    for (int64_t i = 0; i < nseg; ++i) {
-        PRS_TRY(cudaMemcpyAsync(cphi(i), s->phi[s->cur], fbytes, cudaMemcpyDeviceToDevice, st));
-        PRS_TRY(cudaMemcpyAsync(cphi(i) + fbytes, s->dphi, fbytes, cudaMemcpyDeviceToDevice, st));
-        const int64_t len = (i + 1) * K <= nsteps ? K : nsteps - i * K;
-        int rc = prs_step(s, len);
-        if (rc) return rc;
-    }
-    // J and dJ/dphi at the end; dJ/dv = 0 there
     DiagScratch scr = s->scr;
-    PRS_TRY(launch_observable(s, s->phi[s->cur], lphi[0], observable, eps_smooth, scr));
+    if (keep_all) {
+        // forward, writing every state straight into its slot
+        PRS_TRY(cudaMemcpyAsync(ckpt, s->phi[s->cur], fbytes, cudaMemcpyDeviceToDevice, st));
+        PRS_TRY(cudaMemcpyAsync(ckpt + fbytes, s->dphi, fbytes, cudaMemcpyDeviceToDevice, st));
+        for (int64_t k = 0; k < nsteps; ++k) {
+            double c[5];
+            step_coefficients(s->p, n0 + k, c);
+            char* a = ckpt + 2 * fbytes * (size_t)k;
+            char* b = a + 2 * fbytes;
+            PRS_TRY(launch_step_io(s->g, s->p.precision, repro, a, b, a + fbytes, b + fbytes, &c[0], &c[1], &c[2], 1,
+                                   s->rc, err, st));
+        }
+        char* last = ckpt + 2 * fbytes * (size_t)nsteps;
+        PRS_TRY(cudaMemcpyAsync(s->phi[s->cur], last, fbytes, cudaMemcpyDeviceToDevice, st));
+        PRS_TRY(cudaMemcpyAsync(s->dphi, last + fbytes, fbytes, cudaMemcpyDeviceToDevice, st));
+        s->n += nsteps;
+    } else {
+        // forward, keeping a checkpoint at the start of every segment
+        for (int64_t i = 0; i < nseg; ++i) {
+            PRS_TRY(cudaMemcpyAsync(state(0, i), s->phi[s->cur], fbytes, cudaMemcpyDeviceToDevice, st));
+            PRS_TRY(cudaMemcpyAsync(state(0, i) + fbytes, s->dphi, fbytes, cudaMemcpyDeviceToDevice, st));
+            const int64_t len = (i + 1) * K <= nsteps ? K : nsteps - i * K;
+            int rc = prs_step(s, len);
+            if (rc) return rc;
+        }
+    }
+    // J and dJ/dphi at the end; lt = lv + deta lphi = deta dJ/dphi there (lv = 0)
+    PRS_TRY(launch_observable(s, s->phi[s->cur], lphi, lt[0], observable, eps_smooth, scr));
     PRS_TRY(cudaMemcpyAsync(s->h_status, s->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-    PRS_TRY(cudaMemsetAsync(lv[0], 0, fbytes, st));
     int cur = 0;
-    // backward over segments
     for (int64_t i = nseg - 1; i >= 0; --i) {
         const int64_t a = n0 + i * K;
         const int64_t len = (i + 1) * K <= nsteps ? K : nsteps - i * K;
-        for (int64_t k = 0; k + 1 < len; ++k) {  // recompute states a+1 .. a+len-1
-            double c[5];
-            step_coefficients(s->p, a + k, c);
-            PRS_TRY(launch_step_io(s->g, s->p.precision, repro, sphi(k, i), sphi(k + 1, i), sv(k, i), sv(k + 1, i),
-                                   &c[0], &c[1], &c[2], 1, s->rc, err, st));
+        if (!keep_all) {
+            for (int64_t k = 0; k + 1 < len; ++k) {  // recompute states a+1 .. a+len-1
+                double c[5];
+                step_coefficients(s->p, a + k, c);
+                PRS_TRY(launch_step_io(s->g, s->p.precision, repro, state(k, i), state(k + 1, i),
+                                       state(k, i) + fbytes, state(k + 1, i) + fbytes, &c[0], &c[1], &c[2], 1, s->rc,
+                                       err, st));
+            }
         }
         for (int64_t k = len - 1; k >= 0; --k) {
             double c[5];
@@ -307,13 +738,18 @@ extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double ep
             AdjCoef ac{c[0], c[1], c[2], -2.0 / (opd * opd) * c[4], -s->p.deta / (opd * opd) * c[4]};
             DiagScratch sk = scr;
             sk.result = dacc + (a + k - n0);
-            PRS_TRY(launch_adjoint_step(s, sphi(k, i), sv(k, i), lphi[cur], lv[cur], lphi[1 - cur], lv[1 - cur], ac,
-                                        sk));
+            PRS_TRY(launch_adjoint_step(s, state(k, i), state(k, i) + fbytes, lt[cur], lphi, lt[1 - cur], ac,
+                                        a + k == n0, sk, err));
             cur = 1 - cur;
         }
     }
-    if (d_dJ_dphi_init) PRS_TRY(cudaMemcpyAsync(d_dJ_dphi_init, lphi[cur], fbytes, cudaMemcpyDeviceToDevice, st));
-    if (d_dJ_dv_init) PRS_TRY(cudaMemcpyAsync(d_dJ_dv_init, lv[cur], fbytes, cudaMemcpyDeviceToDevice, st));
+    if (d_dJ_dphi_init) PRS_TRY(cudaMemcpyAsync(d_dJ_dphi_init, lphi, fbytes, cudaMemcpyDeviceToDevice, st));
+    if (d_dJ_dv_init) {
+        if (nsteps > 0)
+            PRS_TRY(cudaMemcpyAsync(d_dJ_dv_init, lt[cur], fbytes, cudaMemcpyDeviceToDevice, st));
+        else
+            PRS_TRY(cudaMemsetAsync(d_dJ_dv_init, 0, fbytes, st));
+    }
     if (nsteps > 0)
         PRS_TRY(cudaMemcpyAsync(hacc.data(), dacc, sizeof(DiagAcc) * (size_t)nsteps, cudaMemcpyDeviceToHost, st));
     PRS_TRY(cudaStreamSynchronize(st));

@@ -217,6 +217,7 @@ extern "C" int prs_destroy(prs_sim* s)
         cudaFree(s->dphi);
     }
     cudaFree(s->scr.partials);
+    cudaFree(s->adj_ws);
     cudaFreeHost(s->h_status);
     delete s;
     return PRS_OK;

@@ -23,6 +23,8 @@ struct prs_sim {
     prs::DiagScratch scr;
     prs::DevStatus* d_status; // device: result, counter, error word
     prs::DevStatus* h_status; // pinned host copy
+    void* adj_ws;             // prs_adjoint working memory, kept for the next call
+    size_t adj_ws_bytes;
 };
 
 namespace prs {

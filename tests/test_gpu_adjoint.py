@@ -63,9 +63,11 @@ def test_fp64_adjoint_matches_oracle(shape, obs, nsteps, K):
     assert _rel(end_phi, ophi) <= 1e-12
 
 
-@pytest.mark.parametrize("shape,obs", [((128, 64), 0), ((64, 32, 16), 0), ((128, 32, 8), 1), ((37, 29), 1)])
-def test_fp32_adjoint_matches_oracle(shape, obs):
-    nsteps, K = 20, 8
+@pytest.mark.parametrize("K", [8, 0])
+@pytest.mark.parametrize("shape,obs", [((128, 64), 0), ((64, 32, 16), 0), ((128, 32, 8), 1), ((37, 29), 1),
+                                       ((256, 16, 12), 0), ((512, 40), 1)])
+def test_fp32_adjoint_matches_oracle(shape, obs, K):
+    nsteps = 20
     p = oracle.Params(shape, W0=6.0, eta0=2.0)
     phi0 = (0.8 * inp.random_field(shape, seed=1)).astype(np.float32)
     v0 = (0.05 * inp.random_field(shape, seed=2)).astype(np.float32)
@@ -82,7 +84,8 @@ def test_checkpoint_interval_does_not_change_the_gradient():
     shape = (24, 20, 12)
     phi0 = inp.random_field(shape, seed=5)
     v0 = np.zeros_like(phi0)
-    outs = [_gpu_adjoint(shape, prs.PRS_FP64, phi0, v0, 23, 0, K, flags=prs.PRS_REPRO) for K in (1, 5, 23, 64)]
+    # K = 0: every state kept, no recomputation
+    outs = [_gpu_adjoint(shape, prs.PRS_FP64, phi0, v0, 23, 0, K, flags=prs.PRS_REPRO) for K in (1, 5, 23, 64, 0)]
     for o in outs[1:]:
         assert o[0] == outs[0][0] and o[1] == outs[0][1]
         assert np.array_equal(o[2], outs[0][2]) and np.array_equal(o[3], outs[0][3])
