@@ -78,7 +78,9 @@ typedef struct {
     double phi0;       /* vacuum value (> 0)                                        */
     uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
     uint32_t flags;    /* PRS_REPRO or 0                                            */
-    int32_t tblock;    /* leapfrog steps fused per pass over HBM; 0 = library picks */
+    int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (1);
+                          2 = two-step passes for FP32 3D boxes with an x side that is a
+                          multiple of 128 up to 1024 (else 1); at most 8            */
 } prs_params;
 
 /* One output record of the wall diagnostics (Eq. 7, Eq. 8). */

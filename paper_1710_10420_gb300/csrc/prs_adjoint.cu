@@ -655,8 +655,10 @@ extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double ep
     // one workspace, kept with the run for the next call: [states][lphi, lt[2]][dacc].
     // keep_all: states 0..nsteps back to back; else one checkpoint per segment plus
     // states 1..K-1 of the segment being swept
+    // every array starts on a 256-byte boundary (odd boxes have sizes that are not)
+    const size_t fs = (fbytes + 255) & ~(size_t)255;
     const size_t nstate = keep_all ? (size_t)(nsteps + 1) : (size_t)nseg + (size_t)(K > 1 ? K - 1 : 0);
-    const size_t need = 2 * fbytes * nstate + 3 * fbytes + sizeof(DiagAcc) * (size_t)(nsteps > 0 ? nsteps : 1);
+    const size_t need = 2 * fs * nstate + 3 * fs + sizeof(DiagAcc) * (size_t)(nsteps > 0 ? nsteps : 1);
     if (s->adj_ws_bytes < need) {
         cudaFree(s->adj_ws);
         s->adj_ws = nullptr;
@@ -669,17 +671,17 @@ extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double ep
         s->adj_ws_bytes = need;
     }
     char* ckpt = (char*)s->adj_ws;
-    char* seg = keep_all ? nullptr : ckpt + 2 * fbytes * (size_t)nseg;
-    char* adj = ckpt + 2 * fbytes * nstate;  // lphi, lt[2]
-    DiagAcc* dacc = (DiagAcc*)(adj + 3 * fbytes);
+    char* seg = keep_all ? nullptr : ckpt + 2 * fs * (size_t)nseg;
+    char* adj = ckpt + 2 * fs * nstate;  // lphi, lt[2]
+    DiagAcc* dacc = (DiagAcc*)(adj + 3 * fs);
     std::vector<DiagAcc> hacc((size_t)(nsteps > 0 ? nsteps : 1));
 
-    auto state = [&](int64_t k, int64_t i) -> char* {  // state k (0..K-1) of segment i
-        if (keep_all) return ckpt + 2 * fbytes * (size_t)(i * K + k);
-        return k == 0 ? ckpt + 2 * fbytes * (size_t)i : seg + 2 * fbytes * (size_t)(k - 1);
+    auto state = [&](int64_t k, int64_t i) -> char* {  // phi of state k (0..K-1) of segment i; dphi at + fs
+        if (keep_all) return ckpt + 2 * fs * (size_t)(i * K + k);
+        return k == 0 ? ckpt + 2 * fs * (size_t)i : seg + 2 * fs * (size_t)(k - 1);
     };
     char* lphi = adj;
-    char* lt[2] = {adj + fbytes, adj + 2 * fbytes};
+    char* lt[2] = {adj + fs, adj + 2 * fs};
     unsigned int* err = &s->d_status->error;
     cudaStream_t st = s->stream;
 #define PRS_TRY(call)                                              \
@@ -692,24 +694,24 @@ extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double ep
     if (keep_all) {
         // forward, writing every state straight into its slot
         PRS_TRY(cudaMemcpyAsync(ckpt, s->phi[s->cur], fbytes, cudaMemcpyDeviceToDevice, st));
-        PRS_TRY(cudaMemcpyAsync(ckpt + fbytes, s->dphi, fbytes, cudaMemcpyDeviceToDevice, st));
+        PRS_TRY(cudaMemcpyAsync(ckpt + fs, s->dphi, fbytes, cudaMemcpyDeviceToDevice, st));
         for (int64_t k = 0; k < nsteps; ++k) {
             double c[5];
             step_coefficients(s->p, n0 + k, c);
-            char* a = ckpt + 2 * fbytes * (size_t)k;
-            char* b = a + 2 * fbytes;
-            PRS_TRY(launch_step_io(s->g, s->p.precision, repro, a, b, a + fbytes, b + fbytes, &c[0], &c[1], &c[2], 1,
-                                   s->rc, err, st));
+            char* a = ckpt + 2 * fs * (size_t)k;
+            char* b = a + 2 * fs;
+            PRS_TRY(launch_step_io(s->g, s->p.precision, repro, a, b, a + fs, b + fs, &c[0], &c[1], &c[2], 1, s->rc,
+                                   err, st));
         }
-        char* last = ckpt + 2 * fbytes * (size_t)nsteps;
+        char* last = ckpt + 2 * fs * (size_t)nsteps;
         PRS_TRY(cudaMemcpyAsync(s->phi[s->cur], last, fbytes, cudaMemcpyDeviceToDevice, st));
-        PRS_TRY(cudaMemcpyAsync(s->dphi, last + fbytes, fbytes, cudaMemcpyDeviceToDevice, st));
+        PRS_TRY(cudaMemcpyAsync(s->dphi, last + fs, fbytes, cudaMemcpyDeviceToDevice, st));
         s->n += nsteps;
     } else {
         // forward, keeping a checkpoint at the start of every segment
         for (int64_t i = 0; i < nseg; ++i) {
             PRS_TRY(cudaMemcpyAsync(state(0, i), s->phi[s->cur], fbytes, cudaMemcpyDeviceToDevice, st));
-            PRS_TRY(cudaMemcpyAsync(state(0, i) + fbytes, s->dphi, fbytes, cudaMemcpyDeviceToDevice, st));
+            PRS_TRY(cudaMemcpyAsync(state(0, i) + fs, s->dphi, fbytes, cudaMemcpyDeviceToDevice, st));
             const int64_t len = (i + 1) * K <= nsteps ? K : nsteps - i * K;
             int rc = prs_step(s, len);
             if (rc) return rc;
@@ -726,9 +728,8 @@ extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double ep
             for (int64_t k = 0; k + 1 < len; ++k) {  // recompute states a+1 .. a+len-1
                 double c[5];
                 step_coefficients(s->p, a + k, c);
-                PRS_TRY(launch_step_io(s->g, s->p.precision, repro, state(k, i), state(k + 1, i),
-                                       state(k, i) + fbytes, state(k + 1, i) + fbytes, &c[0], &c[1], &c[2], 1, s->rc,
-                                       err, st));
+                PRS_TRY(launch_step_io(s->g, s->p.precision, repro, state(k, i), state(k + 1, i), state(k, i) + fs,
+                                       state(k + 1, i) + fs, &c[0], &c[1], &c[2], 1, s->rc, err, st));
             }
         }
         for (int64_t k = len - 1; k >= 0; --k) {
@@ -738,7 +739,7 @@ extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double ep
             AdjCoef ac{c[0], c[1], c[2], -2.0 / (opd * opd) * c[4], -s->p.deta / (opd * opd) * c[4]};
             DiagScratch sk = scr;
             sk.result = dacc + (a + k - n0);
-            PRS_TRY(launch_adjoint_step(s, state(k, i), state(k, i) + fbytes, lt[cur], lphi, lt[1 - cur], ac,
+            PRS_TRY(launch_adjoint_step(s, state(k, i), state(k, i) + fs, lt[cur], lphi, lt[1 - cur], ac,
                                         a + k == n0, sk, err));
             cur = 1 - cur;
         }

@@ -122,7 +122,7 @@ extern "C" int prs_default_tblock(const prs_params* params)
     Geo g;
     int rc = check_params(params, &g);
     if (rc) return rc;
-    int t = max_fused_steps(g, params->precision, (params->flags & PRS_REPRO) != 0);
+    int t = default_fused_steps(g, params->precision, (params->flags & PRS_REPRO) != 0);
     return t < 1 ? 1 : t;
 }
 
@@ -217,6 +217,7 @@ extern "C" int prs_destroy(prs_sim* s)
         cudaFree(s->dphi);
     }
     cudaFree(s->scr.partials);
+    cudaFree(s->dphi_alt);
     cudaFree(s->adj_ws);
     cudaFreeHost(s->h_status);
     delete s;
@@ -296,27 +297,45 @@ extern "C" int prs_step(prs_sim* s, int64_t nsteps)
     if (!cfl_ok(s->p, s->n + nsteps - 1)) return PRS_EINVAL;
     const bool repro = (s->p.flags & PRS_REPRO) != 0;
     int tmax = max_fused_steps(s->g, s->p.precision, repro);
-    int tb = s->p.tblock > 0 ? s->p.tblock : tmax;
+    int tb = s->p.tblock > 0 ? s->p.tblock : default_fused_steps(s->g, s->p.precision, repro);
     if (tb > tmax) tb = tmax;
     if (tb < 1) tb = 1;
-    double c1[8], c2[8], cV[8];
-    int64_t done = 0;
-    while (done < nsteps) {
-        int t = (int)((nsteps - done) < tb ? (nsteps - done) : tb);
-        for (int k = 0; k < t; ++k) {
-            double c[5];
-            step_coefficients(s->p, s->n + done + k, c);
-            c1[k] = c[0];
-            c2[k] = c[1];
-            cV[k] = c[2];
+    // Two-step passes read dphi across sites, so they write it to a second buffer;
+    // an even number of them leaves dphi where it started.  The remaining steps
+    // are single-step passes, which update dphi in place.
+    int64_t pairs = tb == 2 ? nsteps / 2 : 0;
+    if (pairs & 1) --pairs;
+    if (pairs > 0 && !s->dphi_alt) {
+        if (cudaMalloc(&s->dphi_alt, (size_t)s->g.S * s->elem) != cudaSuccess) {
+            cudaGetLastError();
+            s->dphi_alt = nullptr;
+            pairs = 0;  // no room for the second buffer: single steps
         }
-        const void* in = s->phi[s->cur];
-        void* out = s->phi[1 - s->cur];
-        cudaError_t e = launch_step(s->g, s->p.precision, repro, in, out, s->dphi, c1, c2, cV, t, s->rc,
-                                    &s->d_status->error, s->stream);
+    }
+    const int64_t singles = nsteps - 2 * pairs;
+    unsigned int* err = &s->d_status->error;
+    for (int64_t k = 0; k < singles; ++k) {
+        double c[5];
+        step_coefficients(s->p, s->n + k, c);
+        cudaError_t e = launch_step(s->g, s->p.precision, repro, s->phi[s->cur], s->phi[1 - s->cur], s->dphi, &c[0],
+                                    &c[1], &c[2], 1, s->rc, err, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
         s->cur = 1 - s->cur;
-        done += t;
+    }
+    const RunConst<float> rcf{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
+                              (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
+    void* vbuf[2] = {s->dphi, s->dphi_alt};
+    for (int64_t k = 0; k < pairs; ++k) {
+        double a[5], b[5];
+        const int64_t n = s->n + singles + 2 * k;
+        step_coefficients(s->p, n, a);
+        step_coefficients(s->p, n + 1, b);
+        cudaError_t e = launch_step_t2(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
+                                       (const float*)vbuf[k & 1], (float*)vbuf[1 - (k & 1)],
+                                       StepCoef<float>{(float)a[0], (float)a[1], (float)a[2]},
+                                       StepCoef<float>{(float)b[0], (float)b[1], (float)b[2]}, rcf, err, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
+        s->cur = 1 - s->cur;
     }
     s->n += nsteps;
     return PRS_OK;

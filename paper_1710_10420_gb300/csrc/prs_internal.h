@@ -74,8 +74,10 @@ cudaError_t launch_step_io(const Geo& g, int precision, bool repro, const void* 
                            const void* dphi_in, void* dphi_out, const double* c1, const double* c2, const double* cV,
                            int nsteps_in_pass, const double run_const[6], unsigned int* err, cudaStream_t st);
 
-// Largest number of steps one launch_step pass can fuse for this geometry/precision.
+// Largest number of steps one pass can fuse for this geometry/precision, and the
+// number used when params.tblock is 0.
 int max_fused_steps(const Geo& g, int precision, bool repro);
+int default_fused_steps(const Geo& g, int precision, bool repro);
 
 cudaError_t launch_measure(const Geo& g, int precision, const void* phi, const void* dphi, const double run_const[6],
                            const DiagScratch& scr, cudaStream_t st);
@@ -84,6 +86,12 @@ cudaError_t launch_measure(const Geo& g, int precision, const void* phi, const v
 bool fast_step_ok(const Geo& g, int precision);
 cudaError_t launch_measure_fast(const Geo& g, const float* phi, const float* v, RunConst<float> rc,
                                 const DiagScratch& scr, unsigned int* err, cudaStream_t st);
+
+// Two fused leapfrog steps per pass (prs_tblock.cu), FP32 3D; dphi out of place.
+bool tblock_ok(const Geo& g, int precision);
+cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
+                           StepCoef<float> k0, StepCoef<float> k1, RunConst<float> rc, unsigned int* err,
+                           cudaStream_t st);
 
 // Store a message for prs_last_error() on this thread.
 void record_error(const char* msg);

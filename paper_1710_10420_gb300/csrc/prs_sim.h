@@ -23,6 +23,7 @@ struct prs_sim {
     prs::DiagScratch scr;
     prs::DevStatus* d_status; // device: result, counter, error word
     prs::DevStatus* h_status; // pinned host copy
+    void* dphi_alt;           // second dphi buffer for passes that read dphi across sites (library-owned)
     void* adj_ws;             // prs_adjoint working memory, kept for the next call
     size_t adj_ws_bytes;
 };

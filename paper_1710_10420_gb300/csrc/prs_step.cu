@@ -8,7 +8,19 @@ cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const v
 cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
                              StepCoef<float> k, RunConst<float> rc, unsigned int* err, cudaStream_t st);
 
+// Steps one pass may fuse (params.tblock above this is clamped).
 int max_fused_steps(const Geo& g, int precision, bool repro)
+{
+    (void)repro;
+    return tblock_ok(g, precision) ? 2 : 1;
+}
+
+// The library's default: one step per pass.  On GB300 the one-step kernel already
+// moves its 16 B per site-update at the measured copy bandwidth, while the two-step
+// kernel (one 512-thread CTA per SM, its rings filling shared memory) is limited
+// by barrier and load latency to about that same rate at 256^3 and 512^3 and runs
+// slower at 1024^3; tblock = 2 selects it explicitly.
+int default_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)g;
     (void)precision;
