@@ -124,14 +124,23 @@ class ClockSampler:
 # ----------------------------------------------------------- distributed
 
 def dist_setup(gpus: int):
+    """Process group for N > 1 replicas (torchrun env); gloo when PRS_BENCH_GLOO is set (CPU tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import datetime
+
         import torch.distributed as dist
 
-        dist.init_process_group("nccl" if os.environ.get("PRS_BENCH_GLOO") is None else "gloo")
+        timeout = datetime.timedelta(seconds=float(os.environ.get("PRS_BENCH_TIMEOUT_S", "600")))
+        dist.init_process_group("nccl" if os.environ.get("PRS_BENCH_GLOO") is None else "gloo", timeout=timeout)
     return world, rank, local
+
+
+def aggregate(units_per_rank: int, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
 
 
 def barrier(world):
@@ -293,8 +302,7 @@ def run_gpu(args, world, rank, local):
     step_ms = sum(a.elapsed_time(b) for a, b in events)
     launch_avg_ms = step_ms / (len(events) * step_launches)
     units_per_launch = 2 if pairs and not singles else 1
-    site_updates = sites * args.interval * args.steps * world
-    value = site_updates / (ms_max / 1e3)
+    value = aggregate(sites * args.interval * args.steps, world, ms_max / 1e3)
 
     peak, peak_kind = peaks()
     achieved = BYTES_PER_SITE_UPDATE[0] * sites * units_per_launch / (launch_avg_ms / 1e3) / 1e9

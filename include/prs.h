@@ -240,6 +240,13 @@ int prs_coefficients(const prs_params* params, int64_t n, double out[5]);
  * when params->tblock is 0 (>= 1), or a negative status for invalid parameters. */
 int prs_default_tblock(const prs_params* params);
 
+/* Self-test of failure detection (no counterpart in the paper).  Launches one
+ * CTA that waits on an mbarrier phase that can never complete (the bounded wait
+ * of the library's kernels, limit 2 s) and spins on a flag nothing sets (limit
+ * 0.2 s).  Both waits must give up; the call then returns PRS_ETIMEOUT, with the
+ * CUDA context still usable, and the error bits seen in *codes (may be NULL). */
+int prs_selftest_wait_timeout(void* stream, unsigned int* codes);
+
 /* Human-readable name of a status code (static string). */
 const char* prs_strerror(int status);
 

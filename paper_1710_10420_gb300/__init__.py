@@ -113,6 +113,7 @@ _SIGS = {
     "prs_destroy": (ctypes.c_int, [_VP]),
     "prs_coefficients": (ctypes.c_int, [_P, ctypes.c_int64, _DP]),
     "prs_default_tblock": (ctypes.c_int, [_P]),
+    "prs_selftest_wait_timeout": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint)]),
     "prs_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
     "prs_batch_run": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64, _DP, ctypes.c_int64]),
     "prs_batch_get_state": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _I64P]),
@@ -301,6 +302,13 @@ def prs_batch_tuning(batch, run: int):
 
 def prs_batch_destroy(batch) -> None:
     _check(load().prs_batch_destroy(batch), "prs_batch_destroy")
+
+
+def prs_selftest_wait_timeout(stream=None):
+    """Returns (status, error bits): PRS_ETIMEOUT when every bounded wait gave up as it should."""
+    codes = ctypes.c_uint()
+    rc = load().prs_selftest_wait_timeout(stream, ctypes.byref(codes))
+    return rc, codes.value
 
 
 def prs_default_tblock(params: prs_params) -> int:
