@@ -265,21 +265,27 @@ def run_gpu(args, world, rank, local):
     sim = prs.Sim(shape, precision=prs.PRS_FP32, stream=stream, device=dev, seed=1000 + rank, tblock=args.tblock)
     sim.init()
     tb = args.tblock if args.tblock > 0 else lib_default_tblock(prs, shape)
-    # kernel launches of one prs_step(interval): two-step passes come in even numbers
-    pairs = (args.interval // 2) & ~1 if tb == 2 else 0
-    singles = args.interval - 2 * pairs
+    # one bench step = the diagnostics of the state at the start of an output interval,
+    # fused into its first leapfrog step (prs_step_measure), then the other interval-1
+    # steps (prs_step); events bracket the two calls separately
+    rest = args.interval - 1
+    pairs = (rest // 2) & ~1 if tb == 2 else 0
+    singles = rest - 2 * pairs
     step_launches = pairs + singles
 
     def one_step(events=None):
-        if events is not None:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            prs.prs_step(sim.handle, args.interval)
-            b.record(stream)
-            events.append((a, b))
-        else:
-            prs.prs_step(sim.handle, args.interval)
-        return prs.prs_measure_ex(sim.handle)
+        if events is None:
+            d = prs.prs_step_measure(sim.handle, 1)
+            prs.prs_step(sim.handle, rest)
+            return d
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        d = prs.prs_step_measure(sim.handle, 1)
+        e[1].record(stream)
+        prs.prs_step(sim.handle, rest)
+        e[2].record(stream)
+        events.append(e)
+        return d
 
     for _ in range(args.warmup):
         one_step()
@@ -298,9 +304,10 @@ def run_gpu(args, world, rank, local):
     ms = start.elapsed_time(stop)
     ms_max = allreduce_max(ms, world, dev)
     # every launch inside the bracketed prs_step calls is the step kernel (for interval = 20:
-    # ten two-step passes or twenty one-step passes), so its mean duration is the total / launches
-    step_ms = sum(a.elapsed_time(b) for a, b in events)
+    # nineteen one-step passes), so its mean duration is the total / launches
+    step_ms = sum(e[1].elapsed_time(e[2]) for e in events)
     launch_avg_ms = step_ms / (len(events) * step_launches)
+    fused_ms = sum(e[0].elapsed_time(e[1]) for e in events) / len(events)
     units_per_launch = 2 if pairs and not singles else 1
     value = aggregate(sites * args.interval * args.steps, world, ms_max / 1e3)
 
@@ -313,7 +320,8 @@ def run_gpu(args, world, rank, local):
                 "algorithmic_bytes_per_launch": BYTES_PER_SITE_UPDATE[0] * sites * units_per_launch,
                 "note": "achieved = 16 B x site-updates of one launch / its mean duration; with two steps per "
                         "pass this effective figure can exceed the copy bandwidth, dram_frac is the measured one",
-                "launch_ms": launch_avg_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+                "launch_ms": launch_avg_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                "fused_step_and_diagnostics_ms": fused_ms}
     if rec:
         roofline["dram_frac"] = rec["dram_bytes_per_launch"] / (launch_avg_ms / 1e3) / 1e9 / peak
 
@@ -324,12 +332,13 @@ def run_gpu(args, world, rank, local):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "shape": list(shape), "interval": args.interval,
+                   "diagnostics": "of the state at the start of each interval, fused into its first step",
                    "fused_steps_per_pass": units_per_launch,
                    "l2": "inputs larger than L2 (state 12 GB)" if sites >= 512 ** 3 else
                    "state comparable to L2; not flushed", "parallelism": f"replicas x{world}",
                    "last_output": {"area_per_volume": d.area_per_volume, "gamma_v": d.gamma_v, "step": d.step}},
         "roofline": roofline, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": args.steps * (step_launches + 1),
+        "gpu_launches": args.steps * (step_launches + 1),  # one fused step+diagnostics launch per interval
     }
     sim.close()
     if rank == 0 and not args.no_batch:
@@ -363,13 +372,12 @@ def run_e2e(args, prs, sim, shape, stream, dev, world) -> dict:
     t0 = time.perf_counter()
     for _ in range(k):
         prs.prs_set_state(sim.handle, h_phi.numpy(), h_v.numpy(), n)
-        prs.prs_step(sim.handle, args.interval)
-        prs.prs_measure_ex(sim.handle)
+        prs.prs_step_measure(sim.handle, args.interval)
     torch.cuda.synchronize(dev)
     secs = allreduce_max(time.perf_counter() - t0, world, dev)
     return {"value": sites * args.interval * k * world / secs, "unit": "site-updates/s",
             "h2d_bytes_per_step": 2 * sites * 4, "d2h_bytes_per_step": 48, "steps": k,
-            "path": "prs_set_state(host) + prs_step + prs_measure"}
+            "path": "prs_set_state(host) + prs_step_measure(interval)"}
 
 
 def ensemble_runs(scale: float = 1.0):

@@ -134,6 +134,13 @@ int prs_measure(prs_sim* sim, double* area_per_volume, double* gamma_v, int64_t*
 /* As prs_measure, filling the whole record. */
 int prs_measure_ex(prs_sim* sim, prs_diag* out);
 
+/* prs_step(nsteps) fused with the diagnostics of the state at the start of the call
+ * (Eq. 7, Eq. 8 on phi^n, dphi^{n-1/2}): for FP32 boxes of the fast path the first
+ * step's pass computes both from one read of the state.  *out receives what
+ * prs_measure_ex would have returned before the call (out->step = n).  nsteps = 0
+ * only measures.  Synchronises at the end. */
+int prs_step_measure(prs_sim* sim, int64_t nsteps, prs_diag* out);
+
 /* Checkpoint: copy the current fields to host arrays (either may be NULL) and the
  * step index to *n (may be NULL).  Synchronises. */
 int prs_get_state(prs_sim* sim, void* h_phi, void* h_dphi, int64_t* n);

@@ -107,6 +107,7 @@ _SIGS = {
     "prs_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "prs_measure": (ctypes.c_int, [_VP, _DP, _DP, _I64P, _I64P]),
     "prs_measure_ex": (ctypes.c_int, [_VP, ctypes.POINTER(prs_diag)]),
+    "prs_step_measure": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(prs_diag)]),
     "prs_get_state": (ctypes.c_int, [_VP, _VP, _VP, _I64P]),
     "prs_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64]),
     "prs_device_state": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I64P]),
@@ -216,6 +217,13 @@ def prs_measure(sim):
 def prs_measure_ex(sim) -> prs_diag:
     d = prs_diag()
     _check(load().prs_measure_ex(sim, ctypes.byref(d)), "prs_measure_ex", ok=(PRS_OK, PRS_ENONFINITE))
+    return d
+
+
+def prs_step_measure(sim, nsteps: int) -> prs_diag:
+    """Diagnostics of the current state, computed inside the first of nsteps steps."""
+    d = prs_diag()
+    _check(load().prs_step_measure(sim, nsteps, ctypes.byref(d)), "prs_step_measure", ok=(PRS_OK, PRS_ENONFINITE))
     return d
 
 

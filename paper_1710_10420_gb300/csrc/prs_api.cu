@@ -387,6 +387,63 @@ static int measure_into(prs_sim* s, prs_diag* d)
     return a.n_nonfinite ? PRS_ENONFINITE : PRS_OK;
 }
 
+// Fill a prs_diag from the device status copied to s->h_status (after a sync).
+static void diag_from_status(const prs_sim* s, int64_t step, prs_diag* d)
+{
+    const DiagAcc& a = s->h_status->result;
+    d->sum_w = a.sum_w;
+    d->sum_ratio = a.sum_ratio;
+    d->n_links = a.n_links;
+    d->n_wall = a.n_wall;
+    d->n_vzero = a.n_vzero;
+    d->n_nonfinite = a.n_nonfinite;
+    d->area_per_volume = a.sum_w / ((double)s->g.S * s->p.dx);
+    int64_t nw = a.n_wall - a.n_vzero;
+    d->gamma_v = nw > 0 ? sqrt(a.sum_ratio / (2.0 * (double)nw)) : 0.0;
+    d->step = step;
+    d->eta = s->p.eta0 + (double)step * s->p.deta;
+}
+
+extern "C" int prs_step_measure(prs_sim* s, int64_t nsteps, prs_diag* out)
+{
+    if (!s || !out || nsteps < 0) return PRS_EINVAL;
+    if (!s->initialised) return PRS_ESTATE;
+    if (nsteps == 0) return measure_into(s, out);
+    if (!cfl_ok(s->p, s->n + nsteps - 1)) return PRS_EINVAL;
+    const int64_t n0 = s->n;
+    cudaError_t e = cudaErrorNotSupported;
+    if (fast_step_ok(s->g, s->p.precision)) {
+        double c[5];
+        step_coefficients(s->p, n0, c);
+        RunConst<float> rc{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
+                           (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
+        e = launch_step_measure_fast(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
+                                     (const float*)s->dphi, (float*)s->dphi,
+                                     StepCoef<float>{(float)c[0], (float)c[1], (float)c[2]}, rc, s->scr,
+                                     &s->d_status->error, s->stream);
+    }
+    if (e == cudaErrorNotSupported) {
+        // no fused kernel for this box: the diagnostics, then the steps
+        int rc = measure_into(s, out);
+        if (rc != PRS_OK && rc != PRS_ENONFINITE) return rc;
+        int rs = prs_step(s, nsteps);
+        if (rs) return rs;
+        PRS_CUDA(cudaStreamSynchronize(s->stream));
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "prs_step_measure launch");
+    s->cur = 1 - s->cur;
+    s->n += 1;
+    PRS_CUDA(cudaMemcpyAsync(s->h_status, s->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s->stream));
+    int rs = prs_step(s, nsteps - 1);
+    if (rs) return rs;
+    PRS_CUDA(cudaStreamSynchronize(s->stream));
+    int err = check_device_error(s);
+    if (err) return err;
+    diag_from_status(s, n0, out);
+    return s->h_status->result.n_nonfinite ? PRS_ENONFINITE : PRS_OK;
+}
+
 extern "C" int prs_measure_ex(prs_sim* s, prs_diag* out)
 {
     if (!s || !out) return PRS_EINVAL;

@@ -73,6 +73,39 @@ __global__ void __launch_bounds__(kFastThreads, 2)
     block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
 }
 
+// One leapfrog step and the diagnostics of its input state from one read of it.
+template <int ITEMS>
+__global__ void __launch_bounds__(kFastThreads, 2)
+    k_step_measure3d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out,
+                         int nx, int ny, int nz, int ty, int cz, StepCoef<float> k, RunConst<float> rc,
+                         DiagScratch scr, unsigned int* err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int ytiles = ny / ty;
+    Tile3D T{phi_in, phi_out, v, v_out, nx, ny, nz, ty, (int)(blockIdx.x % ytiles) * ty,
+             (int)(blockIdx.x / ytiles) * cz, 0};
+    T.zn = min(cz, nz - T.z0);
+    unsigned* wq = reinterpret_cast<unsigned*>(smem_raw + tile_smem3d(nx, ty)) + (threadIdx.x >> 5) * kQueuePerWarp;
+    SiteAcc a{0.0, 0.0, 0.0f, 0.0f, 0, 0, 0, 0};
+    tile3d<ITEMS, true, true>(T, k, rc, smem_raw, wq, a, err);
+    block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kFastThreads, 2)
+    k_step_measure2d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out,
+                         int nx, int ny, int rb, int cy, StepCoef<float> k, RunConst<float> rc, DiagScratch scr,
+                         unsigned int* err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Tile2D T{phi_in, phi_out, v, v_out, nx, ny, rb, (int)blockIdx.x * cy, 0};
+    T.yn = min(cy, ny - T.y0);
+    unsigned* wq = reinterpret_cast<unsigned*>(smem_raw + tile_smem2d(nx, rb)) + (threadIdx.x >> 5) * kQueuePerWarp;
+    SiteAcc a{0.0, 0.0, 0.0f, 0.0f, 0, 0, 0, 0};
+    tile2d<ITEMS, true, true>(T, k, rc, smem_raw, wq, a, err);
+    block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
+}
+
 // ------------------------------------------------------------------ dispatch
 
 static constexpr int kItems = 4;  // float4 per thread per plane: 4096 sites per plane tile
@@ -208,6 +241,51 @@ cudaError_t launch_measure_fast(const Geo& g, const float* phi, const float* v, 
     nchunks = (g.ny + cy - 1) / cy;
     if (nchunks > scr.max_blocks) return cudaErrorNotSupported;
     k_measure2d_f32<kItems><<<nchunks, kFastThreads, sm, st>>>(phi, v, g.nx, g.ny, t, cy, rc, scr, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
+                                     StepCoef<float> k, RunConst<float> rc, const DiagScratch& scr, unsigned int* err,
+                                     cudaStream_t st)
+{
+    static bool attr3 = false, attr2 = false;
+    const int t = kItems * 1024 / g.nx;
+    const int slots = 2 * sm_count();
+    if (g.dims == 3) {
+        const size_t sm = smem3d(g.nx, t) + kQueueBytes;
+        if (sm > kMeasureSmemMax) return cudaErrorNotSupported;
+        if (!attr3) {
+            cudaError_t e = cudaFuncSetAttribute(k_step_measure3d_f32<kItems>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMeasureSmemMax);
+            if (e != cudaSuccess) return e;
+            attr3 = true;
+        }
+        const int ytiles = g.ny / t;
+        if (ytiles > scr.max_blocks) return cudaErrorNotSupported;
+        int nchunks = pick_chunks(ytiles, g.nz, 16, slots, scr.max_blocks);
+        const int cz = (g.nz + nchunks - 1) / nchunks;
+        nchunks = (g.nz + cz - 1) / cz;
+        if ((long long)ytiles * nchunks > scr.max_blocks) return cudaErrorNotSupported;
+        k_step_measure3d_f32<kItems><<<ytiles * nchunks, kFastThreads, sm, st>>>(in, out, v, v_out, g.nx, g.ny, g.nz,
+                                                                                 t, cz, k, rc, scr, err);
+        return cudaGetLastError();
+    }
+    const size_t sm = smem2d(g.nx, t) + kQueueBytes;
+    if (sm > kMeasureSmemMax) return cudaErrorNotSupported;
+    if (!attr2) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_measure2d_f32<kItems>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMeasureSmemMax);
+        if (e != cudaSuccess) return e;
+        attr2 = true;
+    }
+    const int bands = g.ny / t;
+    int nchunks = pick_chunks(1, bands, 4, slots, scr.max_blocks);
+    const int bpc = (bands + nchunks - 1) / nchunks;
+    const int cy = bpc * t;
+    nchunks = (g.ny + cy - 1) / cy;
+    if (nchunks > scr.max_blocks) return cudaErrorNotSupported;
+    k_step_measure2d_f32<kItems><<<nchunks, kFastThreads, sm, st>>>(in, out, v, v_out, g.nx, g.ny, t, cy, k, rc, scr,
+                                                                    err);
     return cudaGetLastError();
 }
 

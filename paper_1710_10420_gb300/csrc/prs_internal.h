@@ -86,6 +86,11 @@ cudaError_t launch_measure(const Geo& g, int precision, const void* phi, const v
 bool fast_step_ok(const Geo& g, int precision);
 cudaError_t launch_measure_fast(const Geo& g, const float* phi, const float* v, RunConst<float> rc,
                                 const DiagScratch& scr, unsigned int* err, cudaStream_t st);
+// One step (in -> out, v -> v_out) and the diagnostics of (in, v); cudaErrorNotSupported
+// when this box has no fused kernel.
+cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
+                                     StepCoef<float> k, RunConst<float> rc, const DiagScratch& scr, unsigned int* err,
+                                     cudaStream_t st);
 
 // Two fused leapfrog steps per pass (prs_tblock.cu), FP32 3D; dphi out of place.
 bool tblock_ok(const Geo& g, int precision);

@@ -242,6 +242,28 @@ def test_measure_tiny_magnitudes(shape):
     assert d["area_per_volume"] == pytest.approx(od.area_per_volume, rel=1e-5)
 
 
+@pytest.mark.parametrize("precision,shape", [(prs.PRS_FP32, (256, 64, 40)), (prs.PRS_FP32, (512, 96)),
+                                             (prs.PRS_FP32, (37, 23)), (prs.PRS_FP64, (32, 24, 16))])
+def test_step_measure_fused(precision, shape):
+    """prs_step_measure = prs_measure_ex of the start state, then prs_step: same numbers, same field."""
+    a = prs.Sim(shape, precision=precision, seed=9)
+    b = prs.Sim(shape, precision=precision, seed=9)
+    a.init().step(7)
+    b.init().step(7)
+    ref = a.measure()
+    a.step(13)
+    d = prs.prs_step_measure(b.handle, 13).as_dict()
+    assert d == ref
+    pa, va, na = a.get_state()
+    pb, vb, nb = b.get_state()
+    a.close()
+    b.close()
+    assert na == nb == 20
+    # the fused kernel evaluates the same expressions, but the compiler may contract
+    # a*b+c into a fused multiply-add differently there: FP32-rounding agreement
+    assert _rel(pb, pa.astype(np.float64)) <= 1e-6 and _rel(vb, va.astype(np.float64)) <= 1e-6
+
+
 def test_measure_nonfinite_and_empty():
     shape = (16, 16)
     sim = prs.Sim(shape, precision=prs.PRS_FP64)
