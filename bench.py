@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the ensemble (batched vs one-at-a-time) figure")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward time figure")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP64 rate and FP32-vs-FP64 figure")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fraction of each ensemble run's steps (1.0: every run to eta = N/2)")
     return ap.parse_args()
@@ -345,6 +346,8 @@ def run_gpu(args, world, rank, local):
         line["batch"] = run_batch_figure(prs, stream, dev, args.batch_scale)
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = run_adjoint_figure(prs, stream, dev)
+    if rank == 0 and not args.no_precision:
+        line["precision"] = run_precision_figure(prs, stream, dev)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.interval)
     if rank == 0:
@@ -482,6 +485,54 @@ def run_adjoint_figure(prs, stream, dev) -> dict:
                    "recomputation and the reverse sweep, with the run's working memory already allocated "
                    "(first_call_s includes allocating it); keep_all stores all 1271 states (163 GB) in HBM")
     return res
+
+
+def run_precision_figure(prs, stream, dev) -> dict:
+    """FP64 step rate and its bound (3D 512^3), and FP32-vs-FP64 diagnostics along one run (2D 512^2)."""
+    import torch
+
+    peak, _ = peaks()
+    shape = (512, 512, 512)
+    sites = int(np.prod(shape))
+    sim = prs.Sim(shape, precision=prs.PRS_FP64, stream=stream, device=dev, seed=2)
+    sim.init()
+    sim.step(2)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim.step(10)
+    z.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(z) / 10
+    sim.close()
+    torch.cuda.empty_cache()
+    fp64 = {"workload": "3D 512^3 FP64 (generic kernel, FMA allowed)", "ms_per_step": ms,
+            "value": sites / (ms / 1e3), "unit": "site-updates/s",
+            "hbm_bound_value": peak * 1e9 / 32.0, "flops_per_site_update": 18,
+            "achieved_fp64_tflops": 18 * sites / (ms / 1e3) / 1e12,
+            "note": "32 B per site-update in FP64; GB300's FP64 rate is far below its FP32 rate"}
+    # FP32 vs FP64 diagnostics of the same initial field, eta 1 -> 256 (2550 steps), every 10 steps
+    shape2 = (512, 512)
+    series = {}
+    for prec in (prs.PRS_FP32, prs.PRS_FP64):
+        sim = prs.Sim(shape2, precision=prec, stream=stream, device=dev, seed=11)
+        sim.init()
+        out = []
+        for _ in range(255):
+            sim.step(10)
+            d = sim.measure()
+            out.append((d["eta"], d["area_per_volume"], d["gamma_v"]))
+        sim.close()
+        series[prec] = np.array(out)
+    f32, f64 = series[prs.PRS_FP32], series[prs.PRS_FP64]
+    rel = np.abs(f32[:, 1:] - f64[:, 1:]) / np.abs(f64[:, 1:])
+    early = f64[:, 0] <= 3.0
+    late = f64[:, 0] > 10.0
+    return {"fp64": fp64, "fp32_vs_fp64": {
+        "workload": "2D 512^2, radiation era, eta 1 -> 256, one seed, outputs every 10 steps",
+        "area_rel_err_eta_le_3_max": float(rel[early, 0].max()), "gamma_v_rel_err_eta_le_3_max": float(rel[early, 1].max()),
+        "area_rel_err_eta_gt_10_median": float(np.median(rel[late, 0])),
+        "gamma_v_rel_err_eta_gt_10_median": float(np.median(rel[late, 1])),
+        "area_rel_err_end": float(rel[-1, 0]), "gamma_v_rel_err_end": float(rel[-1, 1])}}
 
 
 def main():
