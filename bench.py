@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the ensemble (batched vs one-at-a-time) figure")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward time figure")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64 rate and FP32-vs-FP64 figure")
+    ap.add_argument("--no-2d", action="store_true", help="skip the 2D 4096^2 figure")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fraction of each ensemble run's steps (1.0: every run to eta = N/2)")
     return ap.parse_args()
@@ -342,6 +343,8 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": args.steps * (step_launches + 1),  # one fused step+diagnostics launch per interval
     }
     sim.close()
+    if rank == 0 and not args.no_2d and args.workload != "2d4096":
+        line["fig_2d4096"] = run_2d_figure(prs, stream, dev, args.interval)
     if rank == 0 and not args.no_batch:
         line["batch"] = run_batch_figure(prs, stream, dev, args.batch_scale)
     if rank == 0 and not args.no_adjoint:
@@ -485,6 +488,42 @@ def run_adjoint_figure(prs, stream, dev) -> dict:
                    "recomputation and the reverse sweep, with the run's working memory already allocated "
                    "(first_call_s includes allocating it); keep_all stores all 1271 states (163 GB) in HBM")
     return res
+
+
+def run_2d_figure(prs, stream, dev, interval: int) -> dict:
+    """2D 4096^2 FP32 (config 2's box), the same output interval as the main line, 100 intervals."""
+    import torch
+
+    shape = (4096, 4096)
+    sites = shape[0] * shape[1]
+    sim = prs.Sim(shape, stream=stream, device=dev, seed=3)
+    sim.init()
+    for _ in range(5):
+        prs.prs_step_measure(sim.handle, 1)
+        prs.prs_step(sim.handle, interval - 1)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = 100
+    step_ms = 0.0
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for _ in range(k):
+        prs.prs_step_measure(sim.handle, 1)
+        b0.record(stream)
+        prs.prs_step(sim.handle, interval - 1)
+        b1.record(stream)
+        b1.synchronize()
+        step_ms += b0.elapsed_time(b1)
+    z.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(z)
+    sim.close()
+    peak, kind = peaks()
+    launch = step_ms / (k * (interval - 1))
+    return {"workload": "2D 4096^2 FP32 PRS step (5-point), radiation era, 20 steps + FP64 wall diagnostics "
+                        "(state 192 MB: L2-sized, not flushed)",
+            "value": sites * interval * k / (ms / 1e3), "unit": "site-updates/s", "ms_per_step": ms / k,
+            "step_launch_ms": launch, "step_frac_of_copy_bw": 16.0 * sites / (launch / 1e3) / 1e9 / peak}
 
 
 def run_precision_figure(prs, stream, dev) -> dict:
