@@ -89,10 +89,11 @@ struct SiteAcc {
     double sw, sr;
     float pw, pr;  // current plane's partial sums
     int nl, nw, nv0, nnf;
-    __device__ __forceinline__ void fold()
+    // ratio_scale: the factor of the ratio partial (1/V0 for the (dphi/u)^2 form)
+    __device__ __forceinline__ void fold(double ratio_scale)
     {
         sw += (double)pw;
-        sr += (double)pr;
+        sr += (double)pr * ratio_scale;
         pw = 0.0f;
         pr = 0.0f;
     }
@@ -147,15 +148,18 @@ __device__ __forceinline__ void wall_sites4(SiteAcc& a, unsigned wall, float4 c,
         for (int e = 0; e < 4; ++e) a.nnf += (!isfinite(cs[e]) || !isfinite(vs[e])) ? 1 : 0;
     }
     a.nw += __popc(wall);
+    // dphi^2 / V = (dphi/u)^2 / V0 with u = phi^2/phi0^2 - 1: the per-site term is (dphi/u)^2,
+    // and 1/V0 is applied once per plane when the FP32 partial is folded into FP64
+    const bool v0pos = rc.V0 > 0.0f;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const float s = cs[e];
         const float u = ((s - rc.phi0) * (s + rc.phi0)) * rc.inv_phi0sq;
-        const float V = (rc.V0 * u) * u;
         const bool w = (wall >> e) & 1u;
-        const bool pos = V > 0.0f;
+        const bool pos = v0pos && u != 0.0f;
+        const float q = __fdividef(vs[e], u);
         a.nv0 += (w && !pos) ? 1 : 0;
-        a.pr += (w && pos) ? __fdividef(vs[e] * vs[e], V) : 0.0f;
+        a.pr += (w && pos) ? q * q : 0.0f;
     }
 }
 
@@ -265,6 +269,7 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const StepCoef<float>& k
     const int tid = threadIdx.x, lane = tid & 31;
     const int nx = T.nx, ny = T.ny, nz = T.nz, ty = T.ty, y0 = T.y0, z0 = T.z0, zn = T.zn;
     const int nq = nx >> 2;
+    const double rscale = MEAS && rc.V0 > 0.0f ? 1.0 / (double)rc.V0 : 0.0;  // see wall_sites4
     const int tile = (ty + 2) * nx;
     const size_t plane = (size_t)nx * ny;
 
@@ -374,7 +379,7 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const StepCoef<float>& k
                 stg4(vo + off, vc[j]);
             }
         }
-        if (MEAS) a.fold();
+        if (MEAS) a.fold(rscale);
         if (zi + 1 < zn) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];
@@ -396,6 +401,7 @@ __device__ __forceinline__ bool tile2d(const Tile2D& T, const StepCoef<float>& k
     const int nx = T.nx, ny = T.ny, rb = T.rb, y0 = T.y0, yn = T.yn;
     const int nb = yn / rb;
     const int nq = nx >> 2;
+    const double rscale = MEAS && rc.V0 > 0.0f ? 1.0 / (double)rc.V0 : 0.0;  // see wall_sites4
     const int slot = rb * nx;
     const int ringrows = 4 * rb;
     const unsigned rowb = (unsigned)nx * 4u;
@@ -499,7 +505,7 @@ __device__ __forceinline__ bool tile2d(const Tile2D& T, const StepCoef<float>& k
                 stg4(T.v_out + off, vc[j]);
             }
         }
-        if (MEAS) a.fold();
+        if (MEAS) a.fold(rscale);
         if (bi + 1 < nb) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];
