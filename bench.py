@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward time figure")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64 rate and FP32-vs-FP64 figure")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D 4096^2 figure")
+    ap.add_argument("--no-table1", action="store_true", help="skip the scaling-exponent (Table I) figure")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fraction of each ensemble run's steps (1.0: every run to eta = N/2)")
     return ap.parse_args()
@@ -351,6 +352,8 @@ def run_gpu(args, world, rank, local):
         line["adjoint"] = run_adjoint_figure(prs, stream, dev)
     if rank == 0 and not args.no_precision:
         line["precision"] = run_precision_figure(prs, stream, dev)
+    if rank == 0 and not args.no_table1:
+        line["table1"] = run_table1_figure(prs, stream, dev)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.interval)
     if rank == 0:
@@ -550,10 +553,12 @@ def run_precision_figure(prs, stream, dev) -> dict:
             "achieved_fp64_tflops": 18 * sites / (ms / 1e3) / 1e12,
             "note": "32 B per site-update in FP64; GB300's FP64 rate is far below its FP32 rate"}
     # FP32 vs FP64 diagnostics of the same initial field, eta 1 -> 256 (2550 steps), every 10 steps
+    # (FP32 with correctly rounded division and square root in the diagnostics: same fields)
     shape2 = (512, 512)
     series = {}
-    for prec in (prs.PRS_FP32, prs.PRS_FP64):
-        sim = prs.Sim(shape2, precision=prec, stream=stream, device=dev, seed=11)
+    for key, prec, flags in (("fp32", prs.PRS_FP32, 0), ("fp32_cr", prs.PRS_FP32, prs.PRS_FP32_CR),
+                             ("fp64", prs.PRS_FP64, 0)):
+        sim = prs.Sim(shape2, precision=prec, stream=stream, device=dev, seed=11, flags=flags)
         sim.init()
         out = []
         for _ in range(255):
@@ -561,17 +566,93 @@ def run_precision_figure(prs, stream, dev) -> dict:
             d = sim.measure()
             out.append((d["eta"], d["area_per_volume"], d["gamma_v"]))
         sim.close()
-        series[prec] = np.array(out)
-    f32, f64 = series[prs.PRS_FP32], series[prs.PRS_FP64]
-    rel = np.abs(f32[:, 1:] - f64[:, 1:]) / np.abs(f64[:, 1:])
+        series[key] = np.array(out)
+    f64 = series["fp64"]
     early = f64[:, 0] <= 3.0
     late = f64[:, 0] > 10.0
-    return {"fp64": fp64, "fp32_vs_fp64": {
-        "workload": "2D 512^2, radiation era, eta 1 -> 256, one seed, outputs every 10 steps",
-        "area_rel_err_eta_le_3_max": float(rel[early, 0].max()), "gamma_v_rel_err_eta_le_3_max": float(rel[early, 1].max()),
-        "area_rel_err_eta_gt_10_median": float(np.median(rel[late, 0])),
-        "gamma_v_rel_err_eta_gt_10_median": float(np.median(rel[late, 1])),
-        "area_rel_err_end": float(rel[-1, 0]), "gamma_v_rel_err_end": float(rel[-1, 1])}}
+
+    def errs(a, ref):
+        rel = np.abs(a[:, 1:] - ref[:, 1:]) / np.abs(ref[:, 1:])
+        return {"area_rel_err_eta_le_3_max": float(rel[early, 0].max()),
+                "gamma_v_rel_err_eta_le_3_max": float(rel[early, 1].max()),
+                "area_rel_err_eta_gt_10_median": float(np.median(rel[late, 0])),
+                "gamma_v_rel_err_eta_gt_10_median": float(np.median(rel[late, 1])),
+                "area_rel_err_end": float(rel[-1, 0]), "gamma_v_rel_err_end": float(rel[-1, 1])}
+
+    wl = "2D 512^2, radiation era, eta 1 -> 256, one seed, outputs every 10 steps"
+    return {"fp64": fp64, "fp32_vs_fp64": dict(workload=wl, **errs(series["fp32"], f64)),
+            "fp32_cr_vs_fp64": dict(workload=wl + "; FP32 diagnostics with correctly rounded div/sqrt",
+                                    **errs(series["fp32_cr"], f64)),
+            "fp32_vs_fp32_cr": dict(workload=wl + "; identical fields, only the diagnostics' div/sqrt differ",
+                                    **errs(series["fp32"], series["fp32_cr"]))}
+
+
+# Table I of the paper: five seeds each, exponents fitted beyond ln(eta) = 2.58
+TABLE1_PAPER = {"2048^2": {"fp32": {"mu": (-0.9381, 0.0003), "nu": (-0.0374, 0.0005)},
+                           "fp64": {"mu": (-0.9381, 0.0003), "nu": (-0.0374, 0.0005)}},
+                "128^3": {"fp32": {"mu": (-0.956, 0.003), "nu": (-0.034, 0.006)},
+                          "fp64": {"mu": (-0.905, 0.002), "nu": (-0.025, 0.004)}}}
+
+
+def scaling_exponents(series) -> dict:
+    """Eq. 9: per run, least-squares slopes of ln(A/V) and ln(gamma v) against ln(eta) over the
+    outputs with ln(eta) > 2.58; mean over runs and its standard error."""
+    mus, nus = [], []
+    for eta, area, gv in series:
+        m = np.log(eta) > 2.58
+        mus.append(np.polyfit(np.log(eta[m]), np.log(area[m]), 1)[0])
+        nus.append(np.polyfit(np.log(eta[m]), np.log(gv[m]), 1)[0])
+    k = len(mus)
+    return {"mu": float(np.mean(mus)), "mu_err": float(np.std(mus, ddof=1) / np.sqrt(k)),
+            "nu": float(np.mean(nus)), "nu_err": float(np.std(nus, ddof=1) / np.sqrt(k)),
+            "mu_runs": [float(x) for x in mus], "nu_runs": [float(x) for x in nus]}
+
+
+def run_table1_figure(prs, stream, dev, seeds=(1, 2, 3, 4, 5)) -> dict:
+    """Scaling exponents of A/V and gamma v (Eq. 9) from five radiation-era runs of 2D 2048^2 to
+    eta = 1024 and 3D 128^3 to eta = 64, outputs every 10 steps (every unit of eta).  FP32 runs go
+    through the ensemble engine, FP64 runs through prs_step + prs_measure; both start from the
+    same seeded field (exactly representable in FP32)."""
+    import torch
+
+    boxes = {"2048^2": (2048, 2048), "128^3": (128, 128, 128)}
+    every = 10
+    t0 = time.perf_counter()
+    runs = [(name, shape, sd) for name, shape in boxes.items() for sd in seeds]
+    nsteps = [int(round((shape[0] / 2 - 1.0) / 0.1)) for _, shape, _ in runs]
+    b = prs.prs_batch_create([prs.make_params(shape, seed=sd) for _, shape, sd in runs], stream.cuda_stream)
+    out = prs.prs_batch_run(b, nsteps, measure_every=every, out_capacity=max(nsteps) // every + 1)
+    prs.prs_batch_destroy(b)
+    torch.cuda.synchronize(dev)
+    t_fp32 = time.perf_counter() - t0
+    series = {(name, "fp32"): [] for name in boxes}
+    for r, (name, shape, sd) in enumerate(runs):
+        k = nsteps[r] // every + 1
+        o = out[r, :k]
+        series[(name, "fp32")].append((1.0 + 0.1 * o[:, 0], o[:, 1], o[:, 2]))
+    t0 = time.perf_counter()
+    for name, shape in boxes.items():
+        series[(name, "fp64")] = []
+        n = int(round((shape[0] / 2 - 1.0) / 0.1))
+        for sd in seeds:
+            sim = prs.Sim(shape, precision=prs.PRS_FP64, stream=stream, device=dev, seed=sd)
+            sim.init()
+            rows = []
+            for _ in range(n // every + 1):
+                d = prs.prs_measure_ex(sim.handle)
+                rows.append((d.eta, d.area_per_volume, d.gamma_v))
+                if d.step < n:
+                    sim.step(every)
+            sim.close()
+            rows = np.array(rows)
+            series[(name, "fp64")].append((rows[:, 0], rows[:, 1], rows[:, 2]))
+    t_fp64 = time.perf_counter() - t0
+    table = {name: {prec: dict(scaling_exponents(series[(name, prec)]), paper=TABLE1_PAPER[name][prec])
+                    for prec in ("fp32", "fp64")} for name in boxes}
+    return {"workload": "5 seeds (1..5) each of 2D 2048^2 to eta = 1024 and 3D 128^3 to eta = 64, radiation "
+                        "era, white-noise U(-1,1) initial field, FP32 and FP64 from the same field; fit over "
+                        "ln(eta) > 2.58, outputs every unit of eta; error = standard error of the mean",
+            "table": table, "fp32_s": t_fp32, "fp64_s": t_fp64}
 
 
 def main():

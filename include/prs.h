@@ -53,6 +53,15 @@ extern "C" {
  * so that fields are bit-identical to a sequential IEEE-754 double evaluation of
  * Eqs. 3-5; the diagnostic sums are reduced in a fixed order in every mode. */
 #define PRS_REPRO 1u
+/* FP32 only (ignored in FP64, where division and square root are always IEEE):
+ * evaluate the wall diagnostics (Eqs. 7, 8) with correctly rounded division and
+ * square root, as the generic diagnostic kernel does, instead of the fast kernels'
+ * hardware reciprocal square root and approximate division.  The leapfrog step has
+ * no division or square root, so the fields do not change.  Sec. III compares
+ * single precision with and without correctly rounded divide and square root.
+ * prs_step_measure then runs the diagnostics and the steps as separate passes.
+ * Ensembles (prs_batch_create) reject it. */
+#define PRS_FP32_CR 2u
 
 /* Observables of prs_adjoint (not in the paper: smooth stand-ins for Eq. 7). */
 #define PRS_OBS_GRAD_ENERGY 0 /* J = 1/2 sum_s sum_d ((phi_{s+e_d} - phi_s)/dx)^2            */
@@ -77,7 +86,7 @@ typedef struct {
     double W0;         /* wall thickness: V0 = pi^2/(2 W0^2); +inf gives V0 = 0     */
     double phi0;       /* vacuum value (> 0)                                        */
     uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
-    uint32_t flags;    /* PRS_REPRO or 0                                            */
+    uint32_t flags;    /* PRS_REPRO | PRS_FP32_CR, or 0                             */
     int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (1);
                           2 = two-step passes for FP32 3D boxes with an x side that is a
                           multiple of 128 up to 1024 (else 1); at most 8            */

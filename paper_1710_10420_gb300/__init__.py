@@ -28,6 +28,7 @@ PRS_ESTATE = -6
 PRS_FP32 = 0
 PRS_FP64 = 1
 PRS_REPRO = 1
+PRS_FP32_CR = 2
 PRS_OBS_GRAD_ENERGY = 0
 PRS_OBS_SMOOTH_AREA = 1
 

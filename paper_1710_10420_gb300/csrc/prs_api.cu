@@ -89,7 +89,7 @@ static int check_params(const prs_params* pp, Geo* g)
     const prs_params& p = *pp;
     if (p.dims != 2 && p.dims != 3) return PRS_EINVAL;
     if (p.precision != PRS_FP32 && p.precision != PRS_FP64) return PRS_EINVAL;
-    if ((p.flags & ~PRS_REPRO) != 0) return PRS_EINVAL;
+    if ((p.flags & ~(PRS_REPRO | PRS_FP32_CR)) != 0) return PRS_EINVAL;
     int64_t nx = p.N, ny = p.Ny ? p.Ny : p.N, nz = p.dims == 3 ? (p.Nz ? p.Nz : p.N) : 1;
     if (nx < 3 || ny < 3 || (p.dims == 3 && nz < 3)) return PRS_EINVAL;
     if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30)) return PRS_EINVAL;
@@ -355,11 +355,18 @@ int prs::check_device_error(prs_sim* s)
     return PRS_ETIMEOUT;
 }
 
+// The staged FP32 diagnostic kernels (alone or fused into a step) serve this run;
+// PRS_FP32_CR asks for the generic kernel's correctly rounded division and sqrt.
+static bool fast_diag_ok(const prs_sim* s)
+{
+    return fast_step_ok(s->g, s->p.precision) && (s->p.flags & PRS_FP32_CR) == 0;
+}
+
 static int measure_into(prs_sim* s, prs_diag* d)
 {
     if (!s->initialised) return PRS_ESTATE;
     cudaError_t e = cudaErrorNotSupported;
-    if (fast_step_ok(s->g, s->p.precision)) {
+    if (fast_diag_ok(s)) {
         RunConst<float> rc{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
                            (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
         e = launch_measure_fast(s->g, (const float*)s->phi[s->cur], (const float*)s->dphi, rc, s->scr,
@@ -412,7 +419,7 @@ extern "C" int prs_step_measure(prs_sim* s, int64_t nsteps, prs_diag* out)
     if (!cfl_ok(s->p, s->n + nsteps - 1)) return PRS_EINVAL;
     const int64_t n0 = s->n;
     cudaError_t e = cudaErrorNotSupported;
-    if (fast_step_ok(s->g, s->p.precision)) {
+    if (fast_diag_ok(s)) {
         double c[5];
         step_coefficients(s->p, n0, c);
         RunConst<float> rc{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],

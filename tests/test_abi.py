@@ -28,6 +28,18 @@ def test_binding_covers_the_header():
         assert hasattr(prs, n), f"binding lacks {n}"
 
 
+def test_header_constants_match_the_binding():
+    """Every #define PRS_<NAME> value in include/prs.h equals the binding's constant."""
+    import pathlib
+    import re
+
+    text = (pathlib.Path(__file__).resolve().parents[1] / "include" / "prs.h").read_text()
+    found = re.findall(r"^#define\s+(PRS_\w+)\s+\(?(-?\d+)u?\)?", text, flags=re.M)
+    assert len(found) >= 12
+    for name, value in found:
+        assert getattr(prs, name) == int(value), name
+
+
 def test_strerror(lib):
     assert prs.strerror(prs.PRS_OK) == "ok"
     assert prs.strerror(prs.PRS_EINVAL) == "invalid argument"
