@@ -14,12 +14,14 @@
 // dc2/d delta = -deta/(1+delta)^2.
 //
 // The sweep carries lphi (pointwise) and lt (the only adjoint field read across
-// sites): step n reads lt_n with its neighbours, phi^n with its neighbours (for
-// L phi in dJ/dalpha), and dphi^n, lphi_{n+1} pointwise, and writes
+// sites): step n reads lt_n with its neighbours and phi^n, dphi^n, lphi_{n+1} at
+// the site, and writes
 //     lphi_n = lphi_{n+1} + c2 (L lt_n - f'(phi^n) lt_n),  lt_{n-1} = c1 lt_n + deta lphi_n
 // (at the first step of the run it writes lv_n0 = c1 lt_n0 instead): 24 bytes per
-// site in FP32, one pass.  The FP32 kernels stage phi^n and lt_n in shared memory
-// like the forward step (prs_tile.cuh).
+// site in FP32, one pass.  The L phi of dJ/dalpha becomes phi (L lt) in the sum over
+// sites (L is symmetric), so phi is never read across sites in the FP32 kernels,
+// which stage all four fields in shared memory with the TMA engine (prs_tile.cuh
+// does the same for the forward step); the generic kernel keeps the form above.
 //
 // The forward states are either all kept (when they fit in device memory: GB300's
 // HBM holds e.g. 1271 states of a 256^3 FP32 run) or checkpointed every K steps
@@ -119,6 +121,70 @@ __global__ void __launch_bounds__(256) k_observable(const R* __restrict__ phi, R
     block_reduce_and_finish(DiagAcc{J, 0.0, 0, 0, 0, 0}, scr);
 }
 
+// FP32 runs: the same observables with each site's terms in FP32, added to the
+// thread's FP64 sum once per site (FP64 transcendental functions per link would
+// make this pass cost as much as hundreds of steps on this GPU).  For the smooth
+// area, 1 - t_s t_u of two same-sign values near the vacua cancels in FP32; with
+// u = 1 - |tanh x| = 2/(e^{2|x|} + 1) it is u_s + u_u - u_s u_u, which does not, and
+// 1 - t_s^2 = u_s (2 - u_s).
+struct SmoothSign {
+    float t, u;  // tanh(x) and 1 - |tanh(x)|
+};
+
+__device__ __forceinline__ SmoothSign smooth_sign(float x)
+{
+    const float ax = fabsf(x);
+    const float u = ax > 0.5f ? 2.0f / (expf(2.0f * ax) + 1.0f) : 1.0f - tanhf(ax);
+    const float t = ax > 0.5f ? 1.0f - u : tanhf(ax);
+    return SmoothSign{copysignf(t, x), u};
+}
+
+__device__ __forceinline__ float one_minus_tt(const SmoothSign& a, const SmoothSign& b)
+{
+    if ((a.t < 0.0f) != (b.t < 0.0f)) return 1.0f + fabsf(a.t) * fabsf(b.t);
+    return a.u + b.u - a.u * b.u;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_observable_f32(const float* __restrict__ phi, float* __restrict__ grad,
+                                                        float* __restrict__ grad_deta, Geo g, int obs, float inv_eps,
+                                                        float inv_dx2, double jscale, float gscale, float deta,
+                                                        DiagScratch scr)
+{
+    double J = 0.0;
+    PRS_FOR_SITES(g, s, x, y, z)
+    {
+        const Nbr n = neighbours(g, s, x, y, z);
+        const int64_t up[3] = {n.xp, n.yp, n.zp}, dn[3] = {n.xm, n.ym, n.zm};
+        const float ps = phi[s];
+        float js = 0.0f, gr = 0.0f;
+        if (obs == PRS_OBS_GRAD_ENERGY) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const float pu = phi[up[d]], pd = phi[dn[d]];
+                const float gd = pu - ps;
+                js += gd * gd;
+                gr += (ps - pu) + (ps - pd);
+            }
+        } else {
+            const SmoothSign ss = smooth_sign(ps * inv_eps);
+            float nb = 0.0f;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const SmoothSign su = smooth_sign(phi[up[d]] * inv_eps);
+                js += one_minus_tt(ss, su);
+                nb += su.t + smooth_sign(phi[dn[d]] * inv_eps).t;
+            }
+            gr = -(ss.u * (2.0f - ss.u)) * nb;
+        }
+        gr *= gscale;
+        J += (double)js;
+        grad[s] = gr;
+        if (grad_deta) grad_deta[s] = gr * deta;  // lt at the last step: lv = 0 there
+    }
+    block_reduce_and_finish(DiagAcc{J * jscale, 0.0, 0, 0, 0, 0}, scr);
+}
+
 // One reverse step n: lt_in = lt_n, lphi = lphi_{n+1} (updated in place to lphi_n),
 // lt_out = lt_{n-1} (or lv_n at the run's first step, `last`), using the forward
 // state (phi, v) at n; the dJ/dalpha term of this step lands in *scr.result.
@@ -159,7 +225,7 @@ __global__ void __launch_bounds__(256)
 constexpr int kAdjItems = 2;  // float4 per thread per plane: 2048 sites per plane tile
 
 struct AdjTile {
-    const float* phi;    // phi^n (stencil)
+    const float* phi;    // phi^n (pointwise)
     const float* lt_in;  // lt_n (stencil)
     const float* v;      // dphi^n (pointwise)
     float* lphi;         // lphi_{n+1} -> lphi_n (pointwise, in place)
@@ -208,11 +274,15 @@ struct AdjSum {  // per-thread compensated FP32 sum, folded into FP64 once per p
     }
 };
 
-// The pointwise part of one reverse step for 4 sites.
-__device__ __forceinline__ void adj_update4(float4 p, float4 sp, float4 l, float4 sl, float4 vv, float4& lp, float4& out,
+// The pointwise part of one reverse step for 4 sites: p = phi^n, l = lt_n and sl its
+// pair sums, vv = dphi^n, lp = lphi_{n+1} (becomes lphi_n), out = lt_{n-1} (lv_n when
+// last).  The dJ/dalpha sum over sites of lt (dc1 v + dc2 (L phi - f)) is taken as
+// the sum of lt (dc1 v - dc2 f) + dc2 phi (L lt): L is symmetric on the periodic
+// lattice, so the totals are equal, and phi is then needed at the site only.
+__device__ __forceinline__ void adj_update4(float4 p, float4 l, float4 sl, float4 vv, float4& lp, float4& out,
                                             const AdjCoefF& k, const RunConst<float>& rc, bool last, AdjSum& da)
 {
-    const float pc[4] = {p.x, p.y, p.z, p.w}, spc[4] = {sp.x, sp.y, sp.z, sp.w};
+    const float pc[4] = {p.x, p.y, p.z, p.w};
     const float lc[4] = {l.x, l.y, l.z, l.w}, slc[4] = {sl.x, sl.y, sl.z, sl.w};
     const float vc[4] = {vv.x, vv.y, vv.z, vv.w};
     float lpo[4] = {lp.x, lp.y, lp.z, lp.w}, o[4];
@@ -224,16 +294,24 @@ __device__ __forceinline__ void adj_update4(float4 p, float4 sp, float4 l, float
         const float lpn = lpo[e] + k.c2 * (Llt - fprime * lt);
         lpo[e] = lpn;
         o[e] = last ? k.c1 * lt : k.c1 * lt + rc.deta * lpn;
-        const float Lphi = (spc[e] - rc.twoD * q) * rc.inv_dx2;
         const float f = (k.cV * q) * ((q * q) * rc.inv_phi0sq - 1.0f);
-        da.add(lt * (k.dc1 * vc[e] + k.dc2 * (Lphi - f)));
+        da.add(lt * (k.dc1 * vc[e] - k.dc2 * f) + k.dc2 * (q * Llt));
     }
     lp = make_float4(lpo[0], lpo[1], lpo[2], lpo[3]);
     out = make_float4(o[0], o[1], o[2], o[3]);
 }
 
-// 3D: a tile of t rows x len planes; phi^n and lt_n staged plane by plane in two
-// 4-slot rings (one mbarrier per slot counts both copies).
+// Shared memory of the staged sweep: the barriers, a 4-slot ring of lt (read with its
+// neighbours: t+2 rows per 3D plane, t rows per 2D band) and a 2-slot ring holding
+// phi^n, dphi^n and lphi_{n+1} of t rows each (read at the site only).
+__host__ __device__ constexpr size_t adj_smem(int dims, int nx, int t)
+{
+    return 128 + 4 * (size_t)(dims == 3 ? t + 2 : t) * nx * 4 + 2 * 3 * (size_t)t * nx * 4;
+}
+
+// 3D: a tile of t rows x len planes.  Copy i (one mbarrier per lt slot) brings lt
+// plane i of the tile (local: global z0-1+i) and, for i >= 2, the pointwise fields of
+// local plane i-2, which iteration i-2 uses together with lt planes i-2 .. i.
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
     k_adjoint3d_f32(AdjTile T, AdjCoefF k, RunConst<float> rc, bool last, DiagScratch scr, unsigned int* err)
@@ -241,9 +319,10 @@ __global__ void __launch_bounds__(kFastThreads, 2)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     const int nx = T.nx, ny = T.ny, nz = T.nz, ty = T.t;
-    const int tile = (ty + 2) * nx;
-    float* ringP = reinterpret_cast<float*>(smem_raw + 128);
-    float* ringL = ringP + 4 * tile;
+    const int tile = (ty + 2) * nx;  // floats per lt slot
+    const int ptile = ty * nx;       // floats per pointwise field in a slot
+    float* ringL = reinterpret_cast<float*>(smem_raw + 128);
+    float* ringW = ringL + 4 * tile;  // [slot 0..1][phi, dphi, lphi][ptile]
     const int tid = threadIdx.x, lane = tid & 31;
     const int ytiles = ny / ty;
     const int y0 = (blockIdx.x % ytiles) * ty;
@@ -255,6 +334,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
 #pragma unroll
         for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
         mbar_fence_init();
+        fence_proxy_async_global();
     }
     __syncthreads();
     const int ytop = (y0 == 0 ? ny : y0) - 1;
@@ -265,14 +345,19 @@ __global__ void __launch_bounds__(kFastThreads, 2)
         int p = z0 - 1 + i;
         p = p < 0 ? p + nz : (p >= nz ? p - nz : p);
         uint64_t* b = &bar[i & 3];
-        mbar_arrive_expect_tx(b, 2u * rowb * (unsigned)(ty + 2));
-        const float* srcs[2] = {T.phi + (size_t)p * plane, T.lt_in + (size_t)p * plane};
-        float* dsts[2] = {ringP + (i & 3) * tile, ringL + (i & 3) * tile};
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-            bulk_g2s(dsts[f], srcs[f] + (size_t)ytop * nx, rowb, b);
-            bulk_g2s(dsts[f] + nx, srcs[f] + (size_t)y0 * nx, rowb * (unsigned)ty, b);
-            bulk_g2s(dsts[f] + (size_t)(ty + 1) * nx, srcs[f] + (size_t)ybot * nx, rowb, b);
+        const bool pw = i >= 2;
+        mbar_arrive_expect_tx(b, rowb * (unsigned)(ty + 2) + (pw ? 3u * rowb * (unsigned)ty : 0u));
+        float* dst = ringL + (i & 3) * tile;
+        const float* src = T.lt_in + (size_t)p * plane;
+        bulk_g2s(dst, src + (size_t)ytop * nx, rowb, b);
+        bulk_g2s(dst + nx, src + (size_t)y0 * nx, rowb * (unsigned)ty, b);
+        bulk_g2s(dst + (size_t)(ty + 1) * nx, src + (size_t)ybot * nx, rowb, b);
+        if (pw) {
+            const size_t o = (size_t)(z0 + i - 2) * plane + (size_t)y0 * nx;
+            float* w = ringW + ((i - 2) & 1) * 3 * ptile;
+            bulk_g2s(w, T.phi + o, rowb * (unsigned)ty, b);
+            bulk_g2s(w + ptile, T.v + o, rowb * (unsigned)ty, b);
+            bulk_g2s(w + 2 * ptile, T.lphi + o, rowb * (unsigned)ty, b);
         }
     };
     int issued = -1;
@@ -284,15 +369,6 @@ __global__ void __launch_bounds__(kFastThreads, 2)
         int q = tid + kFastThreads * j;
         row[j] = q / nq;
         col[j] = q - row[j] * nq;
-    }
-    float4 vc[ITEMS], lc[ITEMS];
-    {
-        const size_t b0 = (size_t)z0 * plane + (size_t)y0 * nx;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            vc[j] = ldg_stream4(T.v + b0 + (size_t)row[j] * nx + 4 * col[j]);
-            lc[j] = ldg_stream4(T.lphi + b0 + (size_t)row[j] * nx + 4 * col[j]);
-        }
     }
     AdjSum da{0.0, 0.0f, 0.0f};
     for (int zi = 0; zi < zn; ++zi) {
@@ -304,47 +380,30 @@ __global__ void __launch_bounds__(kFastThreads, 2)
             break;
         }
         if (tid == 0 && zi + 3 < nloc) issue(zi + 3), issued = zi + 3;
-        const int z = z0 + zi;
-        float4 vn[ITEMS], ln[ITEMS];
-        if (zi + 1 < zn) {
-            const size_t b1 = (size_t)(z + 1) * plane + (size_t)y0 * nx;
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                vn[j] = ldg_stream4(T.v + b1 + (size_t)row[j] * nx + 4 * col[j]);
-                ln[j] = ldg_stream4(T.lphi + b1 + (size_t)row[j] * nx + 4 * col[j]);
-            }
-        }
         const int sm = (zi & 3) * tile + nx, sc = ((zi + 1) & 3) * tile + nx, sp = ((zi + 2) & 3) * tile + nx;
-        const size_t bz = (size_t)z * plane + (size_t)y0 * nx;
+        const float* w = ringW + (zi & 1) * 3 * ptile;
+        const size_t bz = (size_t)(z0 + zi) * plane + (size_t)y0 * nx;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int off = row[j] * nx + 4 * col[j];
-            float4 P[2], S[2];
-#pragma unroll
-            for (int f = 0; f < 2; ++f) {
-                const float* R = f == 0 ? ringP : ringL;
-                const float4 c = lds4(R + sc + off);
-                float left, right;
-                x_halo(R + sc + row[j] * nx, col[j], nq, nx, lane, c, left, right);
-                P[f] = c;
-                S[f] = pairs4(c, left, right, lds4(R + sc + off + nx), lds4(R + sc + off - nx), lds4(R + sp + off),
-                              lds4(R + sm + off), true);
-            }
-            float4 out;
-            adj_update4(P[0], S[0], P[1], S[1], vc[j], lc[j], out, k, rc, last, da);
-            stg4(T.lphi + bz + off, lc[j]);
+            const float4 c = lds4(ringL + sc + off);
+            float left, right;
+            x_halo(ringL + sc + row[j] * nx, col[j], nq, nx, lane, c, left, right);
+            const float4 S = pairs4(c, left, right, lds4(ringL + sc + off + nx), lds4(ringL + sc + off - nx),
+                                    lds4(ringL + sp + off), lds4(ringL + sm + off), true);
+            float4 lp = lds4(w + 2 * ptile + off), out;
+            adj_update4(lds4(w + off), c, S, lds4(w + ptile + off), lp, out, k, rc, last, da);
+            stg4(T.lphi + bz + off, lp);
             stg4(T.lt_out + bz + off, out);
         }
         da.fold();
-        if (zi + 1 < zn) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j], lc[j] = ln[j];
-        }
     }
     block_reduce_and_finish(DiagAcc{da.tot, 0.0, 0, 0, 0, 0}, scr);
 }
 
-// 2D: a tile of len rows in bands of t rows; band 0 = the row above, nb+1 = below.
+// 2D: a tile of len rows in bands of t rows.  Local lt band 0 is the row above the
+// tile, nb+1 the row below; copy i brings lt band i and, for i >= 2, the pointwise
+// fields of band i-2 of the tile.
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
     k_adjoint2d_f32(AdjTile T, AdjCoefF k, RunConst<float> rc, bool last, DiagScratch scr, unsigned int* err)
@@ -352,9 +411,9 @@ __global__ void __launch_bounds__(kFastThreads, 2)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     const int nx = T.nx, ny = T.ny, rb = T.t;
-    const int slot = rb * nx;
-    float* ringP = reinterpret_cast<float*>(smem_raw + 128);
-    float* ringL = ringP + 4 * slot;
+    const int slot = rb * nx;  // floats per lt slot and per pointwise field in a slot
+    float* ringL = reinterpret_cast<float*>(smem_raw + 128);
+    float* ringW = ringL + 4 * slot;  // [slot 0..1][phi, dphi, lphi][slot]
     const int tid = threadIdx.x, lane = tid & 31;
     const int y0 = blockIdx.x * T.len;
     const int yn = min(T.len, ny - y0);
@@ -366,24 +425,30 @@ __global__ void __launch_bounds__(kFastThreads, 2)
 #pragma unroll
         for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
         mbar_fence_init();
+        fence_proxy_async_global();
     }
     __syncthreads();
     const int nloc = nb + 2;
     auto issue = [&](int i) {
         uint64_t* b = &bar[i & 3];
-        const float* srcs[2] = {T.phi, T.lt_in};
-        float* dsts[2] = {ringP + (i & 3) * slot, ringL + (i & 3) * slot};
+        const bool pw = i >= 2;
+        const unsigned pwb = pw ? 3u * rowb * (unsigned)rb : 0u;
+        float* dst = ringL + (i & 3) * slot;
         if (i == 0 || i == nb + 1) {
             const int y = i == 0 ? (y0 == 0 ? ny : y0) - 1 : ((y0 + yn == ny) ? 0 : y0 + yn);
             const int r = i == 0 ? rb - 1 : 0;
-            mbar_arrive_expect_tx(b, 2u * rowb);
-#pragma unroll
-            for (int f = 0; f < 2; ++f) bulk_g2s(dsts[f] + (size_t)r * nx, srcs[f] + (size_t)y * nx, rowb, b);
+            mbar_arrive_expect_tx(b, rowb + pwb);
+            bulk_g2s(dst + (size_t)r * nx, T.lt_in + (size_t)y * nx, rowb, b);
         } else {
-            const int y = y0 + (i - 1) * rb;
-            mbar_arrive_expect_tx(b, 2u * rowb * (unsigned)rb);
-#pragma unroll
-            for (int f = 0; f < 2; ++f) bulk_g2s(dsts[f], srcs[f] + (size_t)y * nx, rowb * (unsigned)rb, b);
+            mbar_arrive_expect_tx(b, rowb * (unsigned)rb + pwb);
+            bulk_g2s(dst, T.lt_in + (size_t)(y0 + (i - 1) * rb) * nx, rowb * (unsigned)rb, b);
+        }
+        if (pw) {
+            const size_t o = (size_t)(y0 + (i - 2) * rb) * nx;
+            float* w = ringW + ((i - 2) & 1) * 3 * slot;
+            bulk_g2s(w, T.phi + o, rowb * (unsigned)rb, b);
+            bulk_g2s(w + slot, T.v + o, rowb * (unsigned)rb, b);
+            bulk_g2s(w + 2 * slot, T.lphi + o, rowb * (unsigned)rb, b);
         }
     };
     int issued = -1;
@@ -396,13 +461,6 @@ __global__ void __launch_bounds__(kFastThreads, 2)
         row[j] = q / nq;
         col[j] = q - row[j] * nq;
     }
-    float4 vc[ITEMS], lc[ITEMS];
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const size_t o = (size_t)(y0 + row[j]) * nx + 4 * col[j];
-        vc[j] = ldg_stream4(T.v + o);
-        lc[j] = ldg_stream4(T.lphi + o);
-    }
     AdjSum da{0.0, 0.0f, 0.0f};
     for (int bi = 0; bi < nb; ++bi) {
         bool ok = true;
@@ -413,57 +471,39 @@ __global__ void __launch_bounds__(kFastThreads, 2)
             break;
         }
         if (tid == 0 && bi + 3 < nloc) issue(bi + 3), issued = bi + 3;
+        const float* w = ringW + (bi & 1) * 3 * slot;
         const int yb = y0 + bi * rb;
-        float4 vn[ITEMS], ln[ITEMS];
-        if (bi + 1 < nb) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                const size_t o = (size_t)(yb + rb + row[j]) * nx + 4 * col[j];
-                vn[j] = ldg_stream4(T.v + o);
-                ln[j] = ldg_stream4(T.lphi + o);
-            }
-        }
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int lr = (bi + 1) * rb + row[j];
             const int rc0 = (lr % ringrows) * nx, ru = ((lr + ringrows - 1) % ringrows) * nx,
                       rd = ((lr + 1) % ringrows) * nx;
-            float4 P[2], S[2];
-#pragma unroll
-            for (int f = 0; f < 2; ++f) {
-                const float* R = f == 0 ? ringP : ringL;
-                const float4 c = lds4(R + rc0 + 4 * col[j]);
-                float left, right;
-                x_halo(R + rc0, col[j], nq, nx, lane, c, left, right);
-                P[f] = c;
-                const float4 ym = lds4(R + ru + 4 * col[j]), yp = lds4(R + rd + 4 * col[j]);
-                S[f] = pairs4(c, left, right, yp, ym, ym, ym, false);
-            }
-            float4 out;
-            adj_update4(P[0], S[0], P[1], S[1], vc[j], lc[j], out, k, rc, last, da);
-            const size_t o = (size_t)(yb + row[j]) * nx + 4 * col[j];
-            stg4(T.lphi + o, lc[j]);
+            const float4 c = lds4(ringL + rc0 + 4 * col[j]);
+            float left, right;
+            x_halo(ringL + rc0, col[j], nq, nx, lane, c, left, right);
+            const float4 ym = lds4(ringL + ru + 4 * col[j]), yp = lds4(ringL + rd + 4 * col[j]);
+            const float4 S = pairs4(c, left, right, yp, ym, ym, ym, false);
+            const int off = row[j] * nx + 4 * col[j];
+            float4 lp = lds4(w + 2 * slot + off), out;
+            adj_update4(lds4(w + off), c, S, lds4(w + slot + off), lp, out, k, rc, last, da);
+            const size_t o = (size_t)yb * nx + off;
+            stg4(T.lphi + o, lp);
             stg4(T.lt_out + o, out);
         }
         da.fold();
-        if (bi + 1 < nb) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j], lc[j] = ln[j];
-        }
     }
     block_reduce_and_finish(DiagAcc{da.tot, 0.0, 0, 0, 0, 0}, scr);
 }
 
 // FP32 boxes the staged sweep takes: x a multiple of 128 dividing 2048 (2D and 3D),
-// y divisible by the rows of a tile, and the two rings within 113 KB.
+// y divisible by the rows of a tile, and the rings within 113 KB (two CTAs per SM).
 bool adj_fast_ok(const Geo& g, int precision)
 {
     if (precision != PRS_FP32) return false;
     if (g.nx % 128 != 0 || g.nx > kAdjItems * 1024 || (kAdjItems * 1024) % g.nx != 0) return false;
     const int t = kAdjItems * 1024 / g.nx;
     if (g.ny % t != 0) return false;
-    const size_t sm = g.dims == 3 ? 128 + 2 * 4 * (size_t)(t + 2) * g.nx * 4 : 128 + 2 * 4 * (size_t)t * g.nx * 4;
-    return sm <= 113 * 1024;
+    return adj_smem(g.dims, g.nx, t) <= 113 * 1024;
 }
 
 // Grid of the row-wise kernels: x blocks cover a row, y blocks stride over rows;
@@ -493,7 +533,19 @@ cudaError_t launch_observable(const prs_sim* s, const void* phi, void* grad, voi
     k_observable<R, D><<<grid, 256, 0, s->stream>>>((const R*)phi, (R*)grad, (R*)grad_deta, s->g, obs, eps,       \
                                                     s->rc[1], area_scale, s->p.deta, scr)
     if (s->p.precision == PRS_FP32) {
-        if (s->g.dims == 3) PRS_OBS_LAUNCH(float, 3); else PRS_OBS_LAUNCH(float, 2);
+        // J = jscale * sum of the per-site terms, dJ/dphi = gscale * per-site gradient term
+        const bool area = obs == PRS_OBS_SMOOTH_AREA;
+        const double jscale = area ? 0.5 * area_scale : 0.5 * s->rc[1];
+        const float gscale = area ? (float)(0.5 * area_scale / eps) : (float)s->rc[1];
+        const float inv_eps = area ? (float)(1.0 / eps) : 0.0f;
+        if (s->g.dims == 3)
+            k_observable_f32<3><<<grid, 256, 0, s->stream>>>((const float*)phi, (float*)grad, (float*)grad_deta,
+                                                             s->g, obs, inv_eps, (float)s->rc[1], jscale, gscale,
+                                                             (float)s->p.deta, scr);
+        else
+            k_observable_f32<2><<<grid, 256, 0, s->stream>>>((const float*)phi, (float*)grad, (float*)grad_deta,
+                                                             s->g, obs, inv_eps, (float)s->rc[1], jscale, gscale,
+                                                             (float)s->p.deta, scr);
     } else {
         if (s->g.dims == 3) PRS_OBS_LAUNCH(double, 3); else PRS_OBS_LAUNCH(double, 2);
     }
@@ -526,7 +578,7 @@ cudaError_t launch_adjoint_step(const prs_sim* s, const void* phi, const void* v
         AdjCoefF k{(float)c.c1, (float)c.c2, (float)c.cV, (float)c.dc1, (float)c.dc2};
         RunConst<float> rc = run_const<float>(s->rc);
         if (g.dims == 3) {
-            const size_t sm = 128 + 2 * 4 * (size_t)(t + 2) * g.nx * 4;
+            const size_t sm = adj_smem(3, g.nx, t);
             if (!attr3) {
                 cudaError_t e = cudaFuncSetAttribute(k_adjoint3d_f32<kAdjItems>,
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
@@ -550,7 +602,7 @@ cudaError_t launch_adjoint_step(const prs_sim* s, const void* phi, const void* v
             k_adjoint3d_f32<kAdjItems><<<blocks, kFastThreads, sm, s->stream>>>(T, k, rc, last, scr, err);
             return cudaGetLastError();
         }
-        const size_t sm = 128 + 2 * 4 * (size_t)t * g.nx * 4;
+        const size_t sm = adj_smem(2, g.nx, t);
         if (!attr2) {
             cudaError_t e = cudaFuncSetAttribute(k_adjoint2d_f32<kAdjItems>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);

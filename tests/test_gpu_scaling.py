@@ -61,3 +61,39 @@ def test_2d_density_scaling_exponent_band():
     assert abs(mu - (-0.9381)) < 0.08, mus
     # the walls are still there and move (gamma v is unbounded: collapsing domains are fast)
     assert np.all(out[:, -1, 3] > 0) and np.all((out[:, -1, 2] > 0.1) & np.isfinite(out[:, -1, 2]))
+
+
+def _series_fp64(shape, seed, nsteps, every):
+    sim = prs.Sim(shape, precision=prs.PRS_FP64, seed=seed)
+    sim.init()
+    rows = []
+    for _ in range(nsteps // every + 1):
+        d = prs.prs_measure_ex(sim.handle)
+        rows.append((d.eta, d.area_per_volume, d.gamma_v))
+        if d.step < nsteps:
+            sim.step(every)
+    sim.close()
+    return np.array(rows)
+
+
+def _slopes(eta, area, gv):
+    m = np.log(eta) > 2.58
+    return (np.polyfit(np.log(eta[m]), np.log(area[m]), 1)[0], np.polyfit(np.log(eta[m]), np.log(gv[m]), 1)[0])
+
+
+def test_fp32_and_fp64_runs_give_the_same_exponents():
+    """Sec. III, Table I: single and double precision runs from one (FP32-exact) initial field
+    give the same scaling exponents.  2D 1024^2, three seeds, eta 1 -> 512, every unit of eta;
+    the FP32 runs go through the ensemble engine, the FP64 runs through prs_step/prs_measure."""
+    n, seeds, every = 1024, (1, 2, 3), 10
+    nsteps = int(round((n / 2 - 1) / 0.1))
+    b = prs.prs_batch_create([prs.make_params((n, n), seed=s) for s in seeds])
+    out = prs.prs_batch_run(b, [nsteps] * len(seeds), measure_every=every, out_capacity=nsteps // every + 1)
+    prs.prs_batch_destroy(b)
+    for r, s in enumerate(seeds):
+        f64 = _series_fp64((n, n), s, nsteps, every)
+        eta32 = 1.0 + 0.1 * out[r, :, 0]
+        assert np.allclose(eta32, f64[:, 0], rtol=0, atol=1e-9)
+        mu32, nu32 = _slopes(eta32, out[r, :, 1], out[r, :, 2])
+        mu64, nu64 = _slopes(*f64.T)
+        assert abs(mu32 - mu64) < 1e-3 and abs(nu32 - nu64) < 1e-2, (s, mu32, mu64, nu32, nu64)
