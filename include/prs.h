@@ -24,7 +24,10 @@
  *     pointers are CUDA global memory of the current device.
  *   - Work is queued on the stream given at creation (NULL = the legacy default
  *     stream).  Calls that return host results synchronise that stream.
- *   - A handle must not be used from two host threads at once.
+ *   - A handle must not be used from two host threads at once.  Calls on different
+ *     handles may run concurrently from different host threads (each run has its
+ *     own stream; the library keeps no other unsynchronised state), which lets one
+ *     run's host transfers overlap another run's kernels.
  */
 #ifndef PRS_H
 #define PRS_H

@@ -553,37 +553,23 @@ cudaError_t launch_observable(const prs_sim* s, const void* phi, void* grad, voi
     return cudaGetLastError();
 }
 
-int adj_sm_count()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 152;
-    }
-    return n;
-}
-
 cudaError_t launch_adjoint_step(const prs_sim* s, const void* phi, const void* v, const void* lt_in, void* lphi,
                                 void* lt_out, const AdjCoef& c, bool last, DiagScratch scr, unsigned int* err)
 {
     const Geo& g = s->g;
     if (adj_fast_ok(g, s->p.precision)) {
-        static bool attr3 = false, attr2 = false;
+        static std::atomic<unsigned long long> attr3{0}, attr2{0};
         const int t = kAdjItems * 1024 / g.nx;
-        const int slots = 2 * adj_sm_count();
+        const int slots = 2 * sm_count_current();
         AdjTile T{(const float*)phi, (const float*)lt_in, (const float*)v, (float*)lphi, (float*)lt_out,
                   g.nx, g.ny, g.nz, t, 0, 0, 0};
         AdjCoefF k{(float)c.c1, (float)c.c2, (float)c.cV, (float)c.dc1, (float)c.dc2};
         RunConst<float> rc = run_const<float>(s->rc);
         if (g.dims == 3) {
             const size_t sm = adj_smem(3, g.nx, t);
-            if (!attr3) {
-                cudaError_t e = cudaFuncSetAttribute(k_adjoint3d_f32<kAdjItems>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+            {
+                const cudaError_t e = smem_limit_once(attr3, (const void*)k_adjoint3d_f32<kAdjItems>, 113 * 1024);
                 if (e != cudaSuccess) return e;
-                attr3 = true;
             }
             const int ytiles = g.ny / t;
             // z-chunks: whole waves of resident CTAs, chunks of >= 8 planes, one partial per block
@@ -603,11 +589,9 @@ cudaError_t launch_adjoint_step(const prs_sim* s, const void* phi, const void* v
             return cudaGetLastError();
         }
         const size_t sm = adj_smem(2, g.nx, t);
-        if (!attr2) {
-            cudaError_t e = cudaFuncSetAttribute(k_adjoint2d_f32<kAdjItems>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+        {
+            const cudaError_t e = smem_limit_once(attr2, (const void*)k_adjoint2d_f32<kAdjItems>, 113 * 1024);
             if (e != cudaSuccess) return e;
-            attr2 = true;
         }
         const int bands = g.ny / t;
         int nb = (bands + 4 * slots - 1) / (4 * slots);  // bands per tile: about four waves of tiles

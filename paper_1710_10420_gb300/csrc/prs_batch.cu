@@ -243,16 +243,6 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_batch(BatchDev d, int queue
     }
 }
 
-// ------------------------------------------------------------------ host side
-
-int sm_count_dev()
-{
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 152;
-}
-
 }  // namespace
 
 }  // namespace prs
@@ -617,7 +607,7 @@ extern "C" int prs_batch_create(const prs_params* runs, int nruns, void* stream,
         prs_batch_destroy(b);
         return rc;
     }
-    b->grid = per_sm * sm_count_dev();
+    b->grid = per_sm * sm_count_current();
     // fields start from each run's seeded random initial condition; tune, then reset
     for (int r = 0; r < nruns && !rc; ++r)
         rc = batch_cuda(launch_init_random(b->g[r], PRS_FP32, runs[r].seed, b->phi0[r], b->v[r], true, b->stream),

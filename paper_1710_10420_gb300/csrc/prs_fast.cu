@@ -149,31 +149,17 @@ static int pick_chunks(int tiles, int len, int min_len, int slots, long long max
     return best;
 }
 
-static int sm_count()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 152;
-    }
-    return n;
-}
-
 cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
                              StepCoef<float> k, RunConst<float> rc, unsigned int* err, cudaStream_t st)
 {
-    static bool attr3 = false, attr2 = false;
+    static std::atomic<unsigned long long> attr3{0}, attr2{0};
     const int t = kItems * 1024 / g.nx;
-    const int slots = 2 * sm_count();  // two resident CTAs per SM
+    const int slots = 2 * sm_count_current();  // two resident CTAs per SM
     if (g.dims == 3) {
         const size_t sm = smem3d(g.nx, t);
-        if (!attr3) {
-            cudaError_t e = cudaFuncSetAttribute(k_step3d_f32<kItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)kFastSmemMax);
+        {
+            const cudaError_t e = smem_limit_once(attr3, (const void*)k_step3d_f32<kItems>, (int)kFastSmemMax);
             if (e != cudaSuccess) return e;
-            attr3 = true;
         }
         if (sm > kFastSmemMax) return cudaErrorInvalidValue;
         const int ytiles = g.ny / t;
@@ -185,11 +171,9 @@ cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, const fl
         return cudaGetLastError();
     }
     const size_t sm = smem2d(g.nx, t);
-    if (!attr2) {
-        cudaError_t e = cudaFuncSetAttribute(k_step2d_f32<kItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kFastSmemMax);
+    {
+        const cudaError_t e = smem_limit_once(attr2, (const void*)k_step2d_f32<kItems>, (int)kFastSmemMax);
         if (e != cudaSuccess) return e;
-        attr2 = true;
     }
     if (sm > kFastSmemMax) return cudaErrorInvalidValue;
     const int bands = g.ny / t;
@@ -204,17 +188,15 @@ cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, const fl
 cudaError_t launch_measure_fast(const Geo& g, const float* phi, const float* v, RunConst<float> rc,
                                 const DiagScratch& scr, unsigned int* err, cudaStream_t st)
 {
-    static bool attr3 = false, attr2 = false;
+    static std::atomic<unsigned long long> attr3{0}, attr2{0};
     const int t = kItems * 1024 / g.nx;
-    const int slots = 2 * sm_count();
+    const int slots = 2 * sm_count_current();
     if (g.dims == 3) {
         const size_t sm = smem3d(g.nx, t) + kQueueBytes;
         if (sm > kMeasureSmemMax) return cudaErrorNotSupported;
-        if (!attr3) {
-            cudaError_t e = cudaFuncSetAttribute(k_measure3d_f32<kItems>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMeasureSmemMax);
+        {
+            const cudaError_t e = smem_limit_once(attr3, (const void*)k_measure3d_f32<kItems>, (int)kMeasureSmemMax);
             if (e != cudaSuccess) return e;
-            attr3 = true;
         }
         const int ytiles = g.ny / t;
         if (ytiles > scr.max_blocks) return cudaErrorNotSupported;
@@ -228,11 +210,9 @@ cudaError_t launch_measure_fast(const Geo& g, const float* phi, const float* v, 
     }
     const size_t sm = smem2d(g.nx, t) + kQueueBytes;
     if (sm > kMeasureSmemMax) return cudaErrorNotSupported;
-    if (!attr2) {
-        cudaError_t e = cudaFuncSetAttribute(k_measure2d_f32<kItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kMeasureSmemMax);
+    {
+        const cudaError_t e = smem_limit_once(attr2, (const void*)k_measure2d_f32<kItems>, (int)kMeasureSmemMax);
         if (e != cudaSuccess) return e;
-        attr2 = true;
     }
     const int bands = g.ny / t;
     int nchunks = pick_chunks(1, bands, 4, slots, scr.max_blocks);
@@ -248,17 +228,15 @@ cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, 
                                      StepCoef<float> k, RunConst<float> rc, const DiagScratch& scr, unsigned int* err,
                                      cudaStream_t st)
 {
-    static bool attr3 = false, attr2 = false;
+    static std::atomic<unsigned long long> attr3{0}, attr2{0};
     const int t = kItems * 1024 / g.nx;
-    const int slots = 2 * sm_count();
+    const int slots = 2 * sm_count_current();
     if (g.dims == 3) {
         const size_t sm = smem3d(g.nx, t) + kQueueBytes;
         if (sm > kMeasureSmemMax) return cudaErrorNotSupported;
-        if (!attr3) {
-            cudaError_t e = cudaFuncSetAttribute(k_step_measure3d_f32<kItems>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMeasureSmemMax);
+        {
+            const cudaError_t e = smem_limit_once(attr3, (const void*)k_step_measure3d_f32<kItems>, (int)kMeasureSmemMax);
             if (e != cudaSuccess) return e;
-            attr3 = true;
         }
         const int ytiles = g.ny / t;
         if (ytiles > scr.max_blocks) return cudaErrorNotSupported;
@@ -272,11 +250,9 @@ cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, 
     }
     const size_t sm = smem2d(g.nx, t) + kQueueBytes;
     if (sm > kMeasureSmemMax) return cudaErrorNotSupported;
-    if (!attr2) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_measure2d_f32<kItems>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMeasureSmemMax);
+    {
+        const cudaError_t e = smem_limit_once(attr2, (const void*)k_step_measure2d_f32<kItems>, (int)kMeasureSmemMax);
         if (e != cudaSuccess) return e;
-        attr2 = true;
     }
     const int bands = g.ny / t;
     int nchunks = pick_chunks(1, bands, 4, slots, scr.max_blocks);

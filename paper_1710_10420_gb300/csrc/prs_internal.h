@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "prs.h"
 
 namespace prs {
@@ -104,5 +106,17 @@ void record_error(const char* msg);
 // The diagnostic kernel launched on exactly `grid` blocks (1 <= grid <= scr.max_blocks).
 cudaError_t launch_measure_on_grid(const Geo& g, int precision, const void* phi, const void* dphi,
                                    const double run_const[6], const DiagScratch& scr, int grid, cudaStream_t st);
+
+// Host-side setup shared by the launchers.  Calls on different prs_sim handles may
+// run concurrently from several host threads, so neither keeps unsynchronised state.
+
+// Streaming multiprocessors of the current device, cached per device (152 if the
+// query fails).
+int sm_count_current();
+
+// Raise `func`'s dynamic shared-memory limit to `bytes` on the current device, once per
+// device: `done` holds one bit per device ordinal.  Two threads may both make the
+// (idempotent) attribute call; neither skips it before it has succeeded.
+cudaError_t smem_limit_once(std::atomic<unsigned long long>& done, const void* func, int bytes);
 
 }  // namespace prs

@@ -181,19 +181,14 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
                            StepCoef<float> k0, StepCoef<float> k1, RunConst<float> rc, unsigned int* err,
                            cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_step3d_t2<kTbItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kTbSmemMax);
+    static std::atomic<unsigned long long> attr{0};
+    {
+        const cudaError_t e = smem_limit_once(attr, (const void*)k_step3d_t2<kTbItems>, (int)kTbSmemMax);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int ty = pick_ty(g);
     if (ty == 0) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
+    const int sms = sm_count_current();
     const int ytiles = g.ny / ty;
     // z-chunks: whole waves of one CTA per SM, balanced against the four halo planes
     int best = 1;

@@ -378,3 +378,43 @@ def test_full_size_3d_1024_measure_exact_cases():
     b = sim.measure()
     sim.close()
     assert {k: a[k] for k in a if k not in ("step", "eta")} == {k: b[k] for k in b if k not in ("step", "eta")}
+
+
+def test_two_host_threads_on_two_runs():
+    """Calls on different handles may overlap from two host threads (each run has its own
+    stream): every run ends bit-identical to the same run driven alone."""
+    import threading
+
+    import torch
+
+    shapes = [(256, 64, 32), (512, 128)]
+    alone = []
+    for i, shape in enumerate(shapes):
+        sim = prs.Sim(shape, precision=prs.PRS_FP32, seed=40 + i)
+        sim.init()
+        diags = [prs.prs_step_measure(sim.handle, 7).as_dict() for _ in range(6)]
+        alone.append((diags, sim.get_state()))
+        sim.close()
+    sims = [prs.Sim(shape, precision=prs.PRS_FP32, seed=40 + i, stream=torch.cuda.Stream())
+            for i, shape in enumerate(shapes)]
+    out = [None, None]
+    errors = []
+
+    def run(i):
+        try:
+            sims[i].init()
+            out[i] = [prs.prs_step_measure(sims[i].handle, 7).as_dict() for _ in range(6)]
+        except Exception as e:
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for i, sim in enumerate(sims):
+        phi, v, n = sim.get_state()
+        sim.close()
+        assert out[i] == alone[i][0]
+        assert n == alone[i][1][2] and np.array_equal(phi, alone[i][1][0]) and np.array_equal(v, alone[i][1][1])
