@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64 rate and FP32-vs-FP64 figure")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D 4096^2 figure")
     ap.add_argument("--no-table1", action="store_true", help="skip the scaling-exponent (Table I) figure")
+    ap.add_argument("--adjoint-steps", type=int, default=1270, help="leapfrog steps of the adjoint figure")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fraction of each ensemble run's steps (1.0: every run to eta = N/2)")
     return ap.parse_args()
@@ -231,25 +232,29 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_sources_sha() -> str:
+# the sources that define the one-step FP32 kernel (device code and the structs it takes)
+STEP_KERNEL_SOURCES = ("prs_fast.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_reduce.cuh")
+
+
+def kernel_sources_sha(names=STEP_KERNEL_SOURCES) -> str:
     csrc = os.path.join(ROOT, "paper_1710_10420_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in sorted(names):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
 def traffic_record(workload: str):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if it is current."""
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if the kernel's
+    sources are unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get(workload)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("sources_sha") != kernel_sources_sha():
+    if not rec or rec.get("sources_sha") != kernel_sources_sha(tuple(rec.get("sources", STEP_KERNEL_SOURCES))):
         return None
     return rec
 
@@ -349,7 +354,7 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and not args.no_batch:
         line["batch"] = run_batch_figure(prs, stream, dev, args.batch_scale)
     if rank == 0 and not args.no_adjoint:
-        line["adjoint"] = run_adjoint_figure(prs, stream, dev)
+        line["adjoint"] = run_adjoint_figure(prs, stream, dev, args.adjoint_steps)
     if rank == 0 and not args.no_precision:
         line["precision"] = run_precision_figure(prs, stream, dev)
     if rank == 0 and not args.no_table1:
@@ -498,12 +503,12 @@ def run_batch_figure(prs, stream, dev, scale: float) -> dict:
             "tuned_tile_len": tl, "tuned_group_bytes": budget, "first_output_run0": list(out[0, 0])}
 
 
-def run_adjoint_figure(prs, stream, dev) -> dict:
+def run_adjoint_figure(prs, stream, dev, nsteps: int = 1270) -> dict:
     """3D 256^3 FP32: forward to eta = 128 (1270 steps) vs prs_adjoint, checkpoints every 64 steps and
-    (ckpt_every = 0) every state kept in HBM; plus one reverse step vs one forward step."""
+    (ckpt_every = 0) every state kept in HBM."""
     import torch
 
-    shape, nsteps = (256, 256, 256), 1270
+    shape = (256, 256, 256)
     torch.cuda.empty_cache()
     sim = prs.Sim(shape, stream=stream, device=dev, seed=5)
     sim.init()
@@ -514,7 +519,8 @@ def run_adjoint_figure(prs, stream, dev) -> dict:
     torch.cuda.synchronize(dev)
     ms_fwd = a.elapsed_time(z)
     sim.close()
-    res = {"workload": "3D 256^3 FP32, eta 1 -> 128 (1270 steps), J = tanh(phi/0.1)-smoothed wall area",
+    res = {"workload": f"3D 256^3 FP32, eta 1 -> {1 + 0.1 * nsteps:g} ({nsteps} steps), J = tanh(phi/0.1)-smoothed "
+                       "wall area",
            "forward_s": ms_fwd / 1e3}
     for K, key in ((64, "ckpt64"), (0, "keep_all")):
         sim = prs.Sim(shape, stream=stream, device=dev, seed=5)
@@ -534,7 +540,7 @@ def run_adjoint_figure(prs, stream, dev) -> dict:
                     "first_call_s": times[0], "J": J, "dJ_dalpha": dA}
     res["note"] = ("adjoint_s covers the forward pass (with checkpoints or stored states), any segment "
                    "recomputation and the reverse sweep, with the run's working memory already allocated "
-                   "(first_call_s includes allocating it); keep_all stores all 1271 states (163 GB) in HBM")
+                   f"(first_call_s includes allocating it); keep_all stores all {nsteps + 1} states in HBM")
     return res
 
 
