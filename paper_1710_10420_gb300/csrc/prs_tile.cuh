@@ -164,15 +164,18 @@ __device__ __forceinline__ void wall_sites4(SiteAcc& a, unsigned wall, float4 c,
 }
 
 // Crossing links are compacted per warp: each lane appends its links (site e of
-// its float4, axis d) to the warp's queue in shared memory, then the warp takes
-// them 32 at a time, so the link-midpoint gradients cost one pass instead of one
-// divergent pass per site and axis.
-static constexpr int kQueuePerWarp = 32 * 12;  // 4 sites x 3 axes per lane
+// its float4, axis d, item j of the lane's float4s in the plane) to the warp's queue
+// in shared memory, and the warp takes them 32 at a time, so the link-midpoint
+// gradients cost one pass instead of one divergent pass per site and axis.  Full
+// rounds run as soon as 32 links are queued; fewer wait for the next float4, and the
+// plane's remainder runs once at its end.  A queue holds the remainder (< 32) and one
+// float4's links of the whole warp (32 lanes x 4 sites x 3 axes).
+static constexpr int kQueuePerWarp = 32 + 32 * 12;
 static constexpr size_t kQueueBytes = (kFastThreads / 32) * kQueuePerWarp * sizeof(unsigned);
 
-// Appends this lane's set bits of `mask` (bit 4d+e: site e of the float4, axis d) to the warp queue;
-// returns the warp's total.
-__device__ __forceinline__ int enqueue_links(unsigned* wq, unsigned mask, int lane)
+// Appends this lane's set bits of `mask` (bit 4d+e: site e of the float4, axis d) of
+// item j behind the qn pending entries of the warp queue; returns the new count.
+__device__ __forceinline__ int enqueue_links(unsigned* wq, int qn, unsigned mask, int lane, int j)
 {
     const int cnt = __popc(mask);
     int incl = cnt;
@@ -182,51 +185,68 @@ __device__ __forceinline__ int enqueue_links(unsigned* wq, unsigned mask, int la
         if (lane >= o) incl += t;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    int k = incl - cnt;
+    int k = qn + incl - cnt;
     while (mask) {
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
-        wq[k++] = ((unsigned)lane << 4) | (unsigned)b;
+        wq[k++] = ((unsigned)j << 9) | ((unsigned)lane << 4) | (unsigned)b;
     }
     __syncwarp();
-    return total;
+    return qn + total;
 }
 
-// Eq. 7 weight of the link from (x, row r) of plane Pc along axis d (3D).
+// Runs the queued links 32 at a time: all of them when `flush`, else only full
+// rounds, moving the rest to the front.  weight(ent) adds one link's weight.
+// Returns the number of entries left.
+template <typename W>
+__device__ __forceinline__ int run_link_rounds(unsigned* wq, int qn, bool flush, int lane, W&& weight)
+{
+    const int done = flush ? qn : qn & ~31;
+    for (int base = 0; base < done; base += 32)
+        if (base + lane < done) weight(wq[base + lane]);
+    const int rem = qn - done;
+    unsigned keep = 0;
+    if (lane < rem) keep = wq[done + lane];
+    __syncwarp();
+    if (lane < rem) wq[lane] = keep;
+    __syncwarp();
+    return rem;
+}
+
+// Eq. 7 weight of the link from site s = (x, row r) of plane Pc to its +1 neighbour t
+// along axis d (3D).  One round of a warp's link queue holds links along mixed axes,
+// so the axis selects offsets rather than code paths: t = s + o_d, and each transverse
+// axis e adds ((phi(s+e) - phi(s-e)) + (phi(t+e) - phi(t-e)))/4, where t's transverse
+// neighbours sit at the same offsets as s's (x is transverse only when the link is
+// not along x, so s and t share their column).  The components reach link_weight3 in
+// axis order (x, y, z).
 __device__ __forceinline__ float weight3(const float* Pm, const float* Pc, const float* Pp, int r, int x, int d,
                                         int nx)
 {
-    const int xr = x + 1 == nx ? 0 : x + 1, xl = x == 0 ? nx - 1 : x - 1;
-    const float* cm = Pc + (r - 1) * nx;
-    const float* c0 = Pc + r * nx;
-    const float* c1 = Pc + (r + 1) * nx;
-    const float s = c0[x];
-    float gx, gy, gz;
-    if (d == 0) {  // to (x+1, y, z)
-        gx = c0[xr] - s;
-        gy = 0.25f * ((c1[x] - cm[x]) + (c1[xr] - cm[xr]));
-        gz = 0.25f * ((Pp[r * nx + x] - Pm[r * nx + x]) + (Pp[r * nx + xr] - Pm[r * nx + xr]));
-    } else if (d == 1) {  // to (x, y+1, z)
-        gx = 0.25f * ((c0[xr] - c0[xl]) + (c1[xr] - c1[xl]));
-        gy = c1[x] - s;
-        gz = 0.25f * ((Pp[r * nx + x] - Pm[r * nx + x]) + (Pp[(r + 1) * nx + x] - Pm[(r + 1) * nx + x]));
-    } else {  // to (x, y, z+1)
-        const float* p0 = Pp + r * nx;
-        gx = 0.25f * ((c0[xr] - c0[xl]) + (p0[xr] - p0[xl]));
-        gy = 0.25f * ((c1[x] - cm[x]) + (Pp[(r + 1) * nx + x] - Pp[(r - 1) * nx + x]));
-        gz = p0[x] - s;
-    }
-    return link_weight3(gx, gy, gz);
+    const int px = (x + 1 == nx ? 0 : x + 1) - x, mx = (x == 0 ? nx - 1 : x - 1) - x;  // periodic in x
+    const int pz = (int)(Pp - Pc), mz = (int)(Pm - Pc);                                 // ring slots
+    const float* s = Pc + r * nx + x;
+    const float* t = s + (d == 0 ? px : (d == 1 ? nx : pz));
+    const int p1 = d == 0 ? nx : px, m1 = d == 0 ? -nx : mx;  // first transverse axis: y or x
+    const int p2 = d == 2 ? nx : pz, m2 = d == 2 ? -nx : mz;  // second: z, or y for z-links
+    const float gd = *t - *s;
+    const float g1 = 0.25f * ((s[p1] - s[m1]) + (t[p1] - t[m1]));
+    const float g2 = 0.25f * ((s[p2] - s[m2]) + (t[p2] - t[m2]));
+    return link_weight3(d == 0 ? gd : g1, d == 0 ? g1 : (d == 1 ? gd : g2), d == 2 ? gd : g2);
 }
 
-// Eq. 7 weight of the link from x of row crow along axis d (2D); urow/drow are
-// the rows above and below.
+// Eq. 7 weight of the link from x of row crow along axis d (2D); urow/drow are the
+// rows above and below.  Branch-free over d as in weight3.
 __device__ __forceinline__ float weight2(const float* urow, const float* crow, const float* drow, int x, int d, int nx)
 {
-    const int xr = x + 1 == nx ? 0 : x + 1, xl = x == 0 ? nx - 1 : x - 1;
-    const float s = crow[x];
-    if (d == 0) return link_weight2(crow[xr] - s, 0.25f * ((drow[x] - urow[x]) + (drow[xr] - urow[xr])));
-    return link_weight2(0.25f * ((crow[xr] - crow[xl]) + (drow[xr] - drow[xl])), drow[x] - s);
+    const int px = (x + 1 == nx ? 0 : x + 1) - x, mx = (x == 0 ? nx - 1 : x - 1) - x;
+    const int pd = (int)(drow - crow), pu = (int)(urow - crow);
+    const float* s = crow + x;
+    const float* t = s + (d == 0 ? px : pd);
+    const int p1 = d == 0 ? pd : px, m1 = d == 0 ? pu : mx;  // the transverse axis: y or x
+    const float gd = *t - *s;
+    const float g1 = 0.25f * ((s[p1] - s[m1]) + (t[p1] - t[m1]));
+    return link_weight2(d == 0 ? gd : g1, d == 0 ? g1 : gd);
 }
 
 
@@ -339,6 +359,17 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const StepCoef<float>& k
         const float* pp = ring + ((zi + 2) & 3) * tile + nx;
         float* po = T.phi_out + (size_t)z * plane + (size_t)y0 * nx;
         float* vo = T.v_out + (size_t)z * plane + (size_t)y0 * nx;
+        int qn = 0;  // this warp's queued links (MEAS)
+        // one queued link: item j's row and first column are the same in all lanes of
+        // the warp (its 32 float4 are consecutive in one row)
+        auto link3 = [&](unsigned ent) {
+            const int jj = (int)(ent >> 9), b = ent & 15, e = b & 3, d = b >> 2;
+            int r = row[0], cb = col[0];
+#pragma unroll
+            for (int i = 1; i < ITEMS; ++i)
+                if (jj == i) r = row[i], cb = col[i];
+            a.pw += weight3(pm, pc, pp, r, 4 * (cb - lane + (int)((ent >> 4) & 31)) + e, d, nx);
+        };
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int r = row[j];
@@ -360,17 +391,8 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const StepCoef<float>& k
                 // bit 4d+e: the link from site e along axis d crosses
                 const unsigned lmask = lx | (ly << 4) | (lz << 8);
                 a.nl += __popc(lmask);
-                const int total = enqueue_links(wq, lmask, lane);
-                const int colbase = col[j] - lane;  // the warp's 32 float4 are consecutive in one row
-                for (int base = 0; base < total; base += 32) {
-                    const int idx = base + lane;
-                    if (idx < total) {
-                        const unsigned ent = wq[idx];
-                        const int b = ent & 15, e = b & 3, d = b >> 2;
-                        a.pw += weight3(pm, pc, pp, r, 4 * (colbase + (int)(ent >> 4)) + e, d, nx);
-                    }
-                }
-                __syncwarp();
+                qn = enqueue_links(wq, qn, lmask, lane, j);
+                qn = run_link_rounds(wq, qn, false, lane, link3);
             }
             if (STEP) {
                 float4 pn;
@@ -379,7 +401,10 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const StepCoef<float>& k
                 stg4(vo + off, vc[j]);
             }
         }
-        if (MEAS) a.fold(rscale);
+        if (MEAS) {
+            qn = run_link_rounds(wq, qn, true, lane, link3);
+            a.fold(rscale);
+        }
         if (zi + 1 < zn) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];
@@ -465,6 +490,18 @@ __device__ __forceinline__ bool tile2d(const Tile2D& T, const StepCoef<float>& k
             for (int j = 0; j < ITEMS; ++j)
                 vn[j] = ldg_stream4(T.v_in + (size_t)(yb + rb + row[j]) * nx + 4 * col[j]);
         }
+        int qn = 0;  // this warp's queued links (MEAS)
+        auto link2 = [&](unsigned ent) {
+            const int jj = (int)(ent >> 9), b = ent & 15, e = b & 3, d = b >> 2;
+            int r = row[0], cb = col[0];
+#pragma unroll
+            for (int i = 1; i < ITEMS; ++i)
+                if (jj == i) r = row[i], cb = col[i];
+            const int lr = (bi + 1) * rb + r;
+            a.pw += weight2(ring + (size_t)((lr + ringrows - 1) % ringrows) * nx, ring + (size_t)(lr % ringrows) * nx,
+                            ring + (size_t)((lr + 1) % ringrows) * nx, 4 * (cb - lane + (int)((ent >> 4) & 31)) + e, d,
+                            nx);
+        };
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int lr = (bi + 1) * rb + row[j];  // local row of this site in ring order
@@ -485,17 +522,8 @@ __device__ __forceinline__ bool tile2d(const Tile2D& T, const StepCoef<float>& k
                 wall_sites4(a, wall, c, vc[j], rc);
                 const unsigned lmask = lx | (ly << 4);  // bit 4d+e
                 a.nl += __popc(lmask);
-                const int total = enqueue_links(wq, lmask, lane);
-                const int colbase = col[j] - lane;
-                for (int base = 0; base < total; base += 32) {
-                    const int idx = base + lane;
-                    if (idx < total) {
-                        const unsigned ent = wq[idx];
-                        const int b = ent & 15, e = b & 3, d = b >> 2;
-                        a.pw += weight2(urow, crow, drow, 4 * (colbase + (int)(ent >> 4)) + e, d, nx);
-                    }
-                }
-                __syncwarp();
+                qn = enqueue_links(wq, qn, lmask, lane, j);
+                qn = run_link_rounds(wq, qn, false, lane, link2);
             }
             if (STEP) {
                 float4 pn;
@@ -505,7 +533,10 @@ __device__ __forceinline__ bool tile2d(const Tile2D& T, const StepCoef<float>& k
                 stg4(T.v_out + off, vc[j]);
             }
         }
-        if (MEAS) a.fold(rscale);
+        if (MEAS) {
+            qn = run_link_rounds(wq, qn, true, lane, link2);
+            a.fold(rscale);
+        }
         if (bi + 1 < nb) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) vc[j] = vn[j];

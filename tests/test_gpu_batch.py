@@ -154,3 +154,41 @@ def test_batch_rejects_unsupported_runs():
     arr = (prs.prs_params * 1)(*p)
     h = ctypes.c_void_p()
     assert prs.load().prs_batch_create(arr, 1, None, ctypes.byref(h)) == prs.PRS_EINVAL
+
+
+def test_production_box_sizes_match_single_runs():
+    """Matter-era runs at the production box sizes (3D 1024^3, 2D 4096^2) in one ensemble agree
+    with the same runs stepped alone: the diagnostics of the initial field exactly in the counts,
+    later outputs and the final fields to FP32 rounding (the ensemble and the single-run kernels
+    run the same tile routine; the compiler may contract a*b+c differently in each)."""
+    runs = [((1024, 1024, 1024), 2.0, 7), ((4096, 4096), 2.0, 8)]
+    ns, every = 12, 4
+    b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd in runs])
+    try:
+        out = prs.prs_batch_run(b, [ns] * len(runs), measure_every=every, out_capacity=ns // every + 1)
+        states = []
+        for r, (shape, *_rest) in enumerate(runs):
+            phi = np.empty(tuple(reversed(shape)), np.float32)
+            assert prs.prs_batch_get_state(b, r, phi, None) == ns
+            states.append(phi)
+    finally:
+        prs.prs_batch_destroy(b)
+    for r, (shape, era, seed) in enumerate(runs):
+        sim = prs.Sim(shape, precision=prs.PRS_FP32, era_m=era, seed=seed)
+        sim.init()
+        for k in range(ns // every + 1):
+            d = prs.prs_step_measure(sim.handle, every if k < ns // every else 0)
+            assert out[r, k, 0] == every * k == d.step
+            if k == 0:
+                assert out[r, k, 3] == d.n_links
+                assert out[r, k, 1] == pytest.approx(d.area_per_volume, rel=1e-12)
+            else:
+                assert out[r, k, 3] == pytest.approx(d.n_links, rel=1e-5)
+                assert out[r, k, 1] == pytest.approx(d.area_per_volume, rel=1e-5)
+                assert out[r, k, 2] == pytest.approx(d.gamma_v, rel=1e-4)
+        phi, _, n = sim.get_state()
+        sim.close()
+        assert n == ns
+        assert _rel(states[r], phi.astype(np.float64)) <= 1e-6
+        del phi
+        states[r] = None
