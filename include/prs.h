@@ -65,6 +65,17 @@ extern "C" {
  * prs_step_measure then runs the diagnostics and the steps as separate passes.
  * Ensembles (prs_batch_create) reject it. */
 #define PRS_FP32_CR 2u
+/* Checks after every call that queues work (slower; for development):
+ *   - the run's stream is synchronised, so an asynchronous CUDA error is returned
+ *     (PRS_ECUDA) by the call that caused it;
+ *   - a bounded device-side wait that gave up is returned at once (PRS_ETIMEOUT);
+ *   - library-owned fields are allocated between 4 KiB guard bands holding a byte
+ *     pattern; a changed band (a kernel wrote past a field) gives PRS_ECUDA with
+ *     "guard band ... overwritten" in prs_last_error();
+ *   - after a call that changes the state, phi and dphi are scanned: any non-finite
+ *     value gives PRS_ENONFINITE.
+ * Bound (caller-owned) buffers get every check but the guard bands. */
+#define PRS_DEBUG 4u
 
 /* Observables of prs_adjoint (not in the paper: smooth stand-ins for Eq. 7). */
 #define PRS_OBS_GRAD_ENERGY 0 /* J = 1/2 sum_s sum_d ((phi_{s+e_d} - phi_s)/dx)^2            */
@@ -89,7 +100,7 @@ typedef struct {
     double W0;         /* wall thickness: V0 = pi^2/(2 W0^2); +inf gives V0 = 0     */
     double phi0;       /* vacuum value (> 0)                                        */
     uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
-    uint32_t flags;    /* PRS_REPRO | PRS_FP32_CR, or 0                             */
+    uint32_t flags;    /* PRS_REPRO | PRS_FP32_CR | PRS_DEBUG, or 0                 */
     int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (1);
                           2 = two-step passes for FP32 3D boxes with an x side that is a
                           multiple of 128 up to 1024 (else 1); at most 8            */

@@ -29,6 +29,7 @@ PRS_FP32 = 0
 PRS_FP64 = 1
 PRS_REPRO = 1
 PRS_FP32_CR = 2
+PRS_DEBUG = 4
 PRS_OBS_GRAD_ENERGY = 0
 PRS_OBS_SMOOTH_AREA = 1
 

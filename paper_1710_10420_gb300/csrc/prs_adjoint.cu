@@ -644,7 +644,7 @@ struct Scratch {
 
 using namespace prs;
 
-extern "C" int prs_observable(prs_sim* s, int observable, double eps_smooth, double* J)
+static int prs_observable_impl(prs_sim* s, int observable, double eps_smooth, double* J)
 {
     if (!s || !J) return PRS_EINVAL;
     if (observable != PRS_OBS_GRAD_ENERGY && observable != PRS_OBS_SMOOTH_AREA) return PRS_EINVAL;
@@ -663,7 +663,7 @@ extern "C" int prs_observable(prs_sim* s, int observable, double eps_smooth, dou
     return PRS_OK;
 }
 
-extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double eps_smooth, int64_t ckpt_every,
+static int prs_adjoint_impl(prs_sim* s, int64_t nsteps, int observable, double eps_smooth, int64_t ckpt_every,
                            double* J, double* dJ_dalpha, void* d_dJ_dphi_init, void* d_dJ_dv_init)
 {
     if (!s || nsteps < 0 || ckpt_every < 0) return PRS_EINVAL;
@@ -803,4 +803,17 @@ extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double ep
     if (J) *J = Jv;
     if (dJ_dalpha) *dJ_dalpha = da;
     return PRS_OK;
+}
+
+extern "C" int prs_observable(prs_sim* s, int observable, double eps_smooth, double* J)
+{
+    return debug_after(s, prs_observable_impl(s, observable, eps_smooth, J), "prs_observable", false);
+}
+
+extern "C" int prs_adjoint(prs_sim* s, int64_t nsteps, int observable, double eps_smooth, int64_t ckpt_every,
+                           double* J, double* dJ_dalpha, void* d_dJ_dphi_init, void* d_dJ_dv_init)
+{
+    const int rc =
+        prs_adjoint_impl(s, nsteps, observable, eps_smooth, ckpt_every, J, dJ_dalpha, d_dJ_dphi_init, d_dJ_dv_init);
+    return debug_after(s, rc, "prs_adjoint", true);
 }

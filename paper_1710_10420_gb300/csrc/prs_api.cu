@@ -89,7 +89,7 @@ static int check_params(const prs_params* pp, Geo* g)
     const prs_params& p = *pp;
     if (p.dims != 2 && p.dims != 3) return PRS_EINVAL;
     if (p.precision != PRS_FP32 && p.precision != PRS_FP64) return PRS_EINVAL;
-    if ((p.flags & ~(PRS_REPRO | PRS_FP32_CR)) != 0) return PRS_EINVAL;
+    if ((p.flags & ~(PRS_REPRO | PRS_FP32_CR | PRS_DEBUG)) != 0) return PRS_EINVAL;
     int64_t nx = p.N, ny = p.Ny ? p.Ny : p.N, nz = p.dims == 3 ? (p.Nz ? p.Nz : p.N) : 1;
     if (nx < 3 || ny < 3 || (p.dims == 3 && nz < 3)) return PRS_EINVAL;
     if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30)) return PRS_EINVAL;
@@ -161,9 +161,11 @@ extern "C" int prs_create(const prs_params* params, void* stream, prs_sim** out)
     s->scr.result = &s->d_status->result;
     s->scr.counter = &s->d_status->counter;
     if (cudaMemset(blob, 0, bytes) != cudaSuccess ||
-        cudaMallocHost((void**)&s->h_status, sizeof(DevStatus)) != cudaSuccess) {
+        cudaMallocHost((void**)&s->h_status, sizeof(DevStatus)) != cudaSuccess ||
+        ((params->flags & PRS_DEBUG) && cudaMalloc((void**)&s->d_dbg, sizeof(DebugCheck)) != cudaSuccess)) {
         int r = cuda_fail(cudaGetLastError(), "prs_create");
         cudaFree(blob);
+        cudaFreeHost(s->h_status);
         delete s;
         return r;
     }
@@ -189,6 +191,23 @@ int prs::ensure_buffers(prs_sim* s)
 {
     if (s->have_buffers) return PRS_OK;
     size_t bytes = (size_t)s->g.S * s->elem;
+    if (s->p.flags & PRS_DEBUG) {
+        void* f[3] = {nullptr, nullptr, nullptr};
+        for (int i = 0; i < 3; ++i) {
+            int rc = debug_alloc_field(bytes, &s->guard_base[i], &f[i]);
+            if (rc) {
+                for (int k = 0; k < i; ++k) cudaFree(s->guard_base[k]), s->guard_base[k] = nullptr;
+                return rc;
+            }
+        }
+        s->phi[0] = f[0];
+        s->phi[1] = f[1];
+        s->dphi = f[2];
+        s->cur = 0;
+        s->owned = true;
+        s->have_buffers = true;
+        return PRS_OK;
+    }
     void *a = nullptr, *b = nullptr, *v = nullptr;
     if (cudaMalloc(&a, bytes) != cudaSuccess || cudaMalloc(&b, bytes) != cudaSuccess ||
         cudaMalloc(&v, bytes) != cudaSuccess) {
@@ -211,11 +230,14 @@ extern "C" int prs_destroy(prs_sim* s)
 {
     if (!s) return PRS_EINVAL;
     cudaStreamSynchronize(s->stream);
-    if (s->owned) {
+    if (s->owned && (s->p.flags & PRS_DEBUG)) {
+        for (int i = 0; i < 3; ++i) cudaFree(s->guard_base[i]);
+    } else if (s->owned) {
         cudaFree(s->phi[0]);
         cudaFree(s->phi[1]);
         cudaFree(s->dphi);
     }
+    cudaFree(s->d_dbg);
     cudaFree(s->scr.partials);
     cudaFree(s->dphi_alt);
     cudaFree(s->adj_ws);
@@ -226,7 +248,7 @@ extern "C" int prs_destroy(prs_sim* s)
 
 // ------------------------------------------------------------------ state
 
-extern "C" int prs_init(prs_sim* s, const void* h_phi, const void* h_dphi)
+static int prs_init_impl(prs_sim* s, const void* h_phi, const void* h_dphi)
 {
     if (!s) return PRS_EINVAL;
     int rc = ensure_buffers(s);
@@ -251,7 +273,7 @@ extern "C" int prs_init(prs_sim* s, const void* h_phi, const void* h_dphi)
     return PRS_OK;
 }
 
-extern "C" int prs_set_state(prs_sim* s, const void* h_phi, const void* h_dphi, int64_t n)
+static int prs_set_state_impl(prs_sim* s, const void* h_phi, const void* h_dphi, int64_t n)
 {
     if (!s || !h_phi || !h_dphi || n < 0) return PRS_EINVAL;
     int rc = ensure_buffers(s);
@@ -320,7 +342,7 @@ cudaError_t prs::smem_limit_once(std::atomic<unsigned long long>& done, const vo
 
 // ------------------------------------------------------------------- step
 
-extern "C" int prs_step(prs_sim* s, int64_t nsteps)
+static int prs_step_impl(prs_sim* s, int64_t nsteps)
 {
     if (!s || nsteps < 0) return PRS_EINVAL;
     if (!s->initialised) return PRS_ESTATE;
@@ -442,7 +464,7 @@ static void diag_from_status(const prs_sim* s, int64_t step, prs_diag* d)
     d->eta = s->p.eta0 + (double)step * s->p.deta;
 }
 
-extern "C" int prs_step_measure(prs_sim* s, int64_t nsteps, prs_diag* out)
+static int prs_step_measure_impl(prs_sim* s, int64_t nsteps, prs_diag* out)
 {
     if (!s || !out || nsteps < 0) return PRS_EINVAL;
     if (!s->initialised) return PRS_ESTATE;
@@ -482,13 +504,13 @@ extern "C" int prs_step_measure(prs_sim* s, int64_t nsteps, prs_diag* out)
     return s->h_status->result.n_nonfinite ? PRS_ENONFINITE : PRS_OK;
 }
 
-extern "C" int prs_measure_ex(prs_sim* s, prs_diag* out)
+static int prs_measure_ex_impl(prs_sim* s, prs_diag* out)
 {
     if (!s || !out) return PRS_EINVAL;
     return measure_into(s, out);
 }
 
-extern "C" int prs_measure(prs_sim* s, double* area_per_volume, double* gamma_v, int64_t* n_links,
+static int prs_measure_impl(prs_sim* s, double* area_per_volume, double* gamma_v, int64_t* n_links,
                            int64_t* n_wall_sites)
 {
     if (!s) return PRS_EINVAL;
@@ -500,4 +522,37 @@ extern "C" int prs_measure(prs_sim* s, double* area_per_volume, double* gamma_v,
     if (n_links) *n_links = d.n_links;
     if (n_wall_sites) *n_wall_sites = d.n_wall;
     return rc;
+}
+
+// ------------------------------------------------ entry points (PRS_DEBUG checks)
+
+extern "C" int prs_init(prs_sim* s, const void* h_phi, const void* h_dphi)
+{
+    return debug_after(s, prs_init_impl(s, h_phi, h_dphi), "prs_init", true);
+}
+
+extern "C" int prs_set_state(prs_sim* s, const void* h_phi, const void* h_dphi, int64_t n)
+{
+    return debug_after(s, prs_set_state_impl(s, h_phi, h_dphi, n), "prs_set_state", true);
+}
+
+extern "C" int prs_step(prs_sim* s, int64_t nsteps)
+{
+    return debug_after(s, prs_step_impl(s, nsteps), "prs_step", true);
+}
+
+extern "C" int prs_step_measure(prs_sim* s, int64_t nsteps, prs_diag* out)
+{
+    return debug_after(s, prs_step_measure_impl(s, nsteps, out), "prs_step_measure", true);
+}
+
+extern "C" int prs_measure_ex(prs_sim* s, prs_diag* out)
+{
+    return debug_after(s, prs_measure_ex_impl(s, out), "prs_measure_ex", false);
+}
+
+extern "C" int prs_measure(prs_sim* s, double* area_per_volume, double* gamma_v, int64_t* n_links, int64_t* n_wall_sites)
+{
+    const int rc = prs_measure_impl(s, area_per_volume, gamma_v, n_links, n_wall_sites);
+    return debug_after(s, rc, "prs_measure", false);
 }

@@ -61,6 +61,14 @@ struct DevStatus {
     unsigned int error;
 };
 
+// PRS_DEBUG: guard bands around library-owned fields and the scan's results.
+static constexpr size_t kGuardBytes = 4096;
+static constexpr unsigned char kGuardByte = 0xA5;
+struct DebugCheck {
+    unsigned int bad_guard;       // bit b: guard band b differs from the pattern
+    unsigned long long nonfinite; // non-finite values in phi^n and dphi
+};
+
 // Kernel launchers (prs_kernels.cu).  Each returns cudaSuccess or the launch error.
 cudaError_t launch_init_random(const Geo& g, int precision, uint64_t seed, void* phi, void* dphi, bool zero_dphi,
                                cudaStream_t st);

@@ -26,6 +26,8 @@ struct prs_sim {
     void* dphi_alt;           // second dphi buffer for passes that read dphi across sites (library-owned)
     void* adj_ws;             // prs_adjoint working memory, kept for the next call
     size_t adj_ws_bytes;
+    void* guard_base[3];      // PRS_DEBUG: allocations of phi[0], phi[1], dphi with guard bands
+    prs::DebugCheck* d_dbg;   // PRS_DEBUG: results of the scan kernel
 };
 
 namespace prs {
@@ -40,5 +42,10 @@ int cuda_fail(cudaError_t e, const char* what);
 int ensure_buffers(prs_sim* s);
 // After a synchronised read of s->h_status: PRS_ETIMEOUT (once) if a device wait gave up.
 int check_device_error(prs_sim* s);
+// PRS_DEBUG: the checks after a call that returned rc (prs_debug.cu); scan_state adds
+// the non-finite scan of the state.  Returns rc when the run has no PRS_DEBUG.
+int debug_after(prs_sim* s, int rc, const char* where, bool scan_state);
+// PRS_DEBUG: one field of `bytes` between two guard bands.
+int debug_alloc_field(size_t bytes, void** base, void** field);
 
 }  // namespace prs
