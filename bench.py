@@ -1,8 +1,8 @@
 """Benchmark of the PRS hot path on GB300: site-updates/s and the HBM roofline fraction.
 
 One benchmark step = one output interval of the paper's runs: ``--interval`` (20)
-leapfrog steps (Eqs. 3-6) followed by the wall diagnostics (Eq. 7, Eq. 8) reduced in
-FP64 and read back on the host.  Default workload: 3D 1024^3 FP32, PRS (alpha=3,
+leapfrog steps (Eqs. 3-6), the first of them fused with the wall diagnostics (Eq. 7,
+Eq. 8) of the state it reads, reduced in FP64 and read back on the host.  Default workload: 3D 1024^3 FP32, PRS (alpha=3,
 beta=0), radiation era, deta=0.1, seeded uniform(-1,1) initial field.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 3d1024|2d4096|3d512]
