@@ -280,7 +280,8 @@ int prs_selftest_wait_timeout(void* stream, unsigned int* codes);
 /* Human-readable name of a status code (static string). */
 const char* prs_strerror(int status);
 
-/* Last CUDA error text seen by the library on this thread (static buffer). */
+/* Text of the last error the library recorded on this thread: a failed CUDA call,
+ * a bounded wait that gave up, or a PRS_DEBUG check (static buffer). */
 const char* prs_last_error(void);
 
 #ifdef __cplusplus
