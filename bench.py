@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--workload", default="3d1024", choices=sorted(WORKLOADS))
     ap.add_argument("--interval", type=int, default=20, help="leapfrog steps per diagnostic output")
     ap.add_argument("--tblock", type=int, default=0, help="fused steps per HBM pass (0: library default)")
-    ap.add_argument("--e2e-steps", type=int, default=24)
+    ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the ensemble (batched vs one-at-a-time) figure")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward time figure")
