@@ -15,16 +15,17 @@ int max_fused_steps(const Geo& g, int precision, bool repro)
     return tblock_ok(g, precision) ? 2 : 1;
 }
 
-// The library's default: one step per pass.  On GB300 the one-step kernel already
-// moves its 16 B per site-update at the measured copy bandwidth, while the two-step
-// kernel (one 512-thread CTA per SM, its rings filling shared memory) is limited
-// by barrier and load latency to about that same rate at 256^3 and 512^3 and runs
-// slower at 1024^3; tblock = 2 selects it explicitly.
+// The library's default.  3D: one step per pass — the one-step kernel already moves
+// its 16 B per site-update at the measured copy bandwidth, while the two-step kernel (one
+// 512-thread CTA per SM, its rings filling shared memory) is limited by barrier and load
+// latency to about that same rate at 256^3 and 512^3 and runs slower at 1024^3.  2D: two
+// steps per pass once the state (three fields) outgrows L2 — rows are whole, so level 1
+// recomputes only the two rows outside each chunk (4096^2: 29 us against 48 us per step);
+// an L2-resident state (2048^2) steps faster one step at a time.
 int default_fused_steps(const Geo& g, int precision, bool repro)
 {
-    (void)g;
-    (void)precision;
     (void)repro;
+    if (g.dims == 2 && precision == PRS_FP32 && tblock_ok(g, precision) && g.S >= (int64_t)1 << 24) return 2;
     return 1;
 }
 

@@ -1,4 +1,4 @@
-// prs_tblock.cu -- two leapfrog steps (Eqs. 3-5) per pass over HBM, FP32 3D.
+// prs_tblock.cu -- two leapfrog steps (Eqs. 3-5) per pass over HBM, FP32 3D and 2D.
 //
 // One pass reads phi^n, dphi^{n-1/2} once and writes phi^{n+2}, dphi^{n+3/2} once:
 // 16 bytes per two site-updates.  A CTA owns ty whole x-rows of y and a chunk of
@@ -153,6 +153,142 @@ __global__ void __launch_bounds__(kTbThreads, 1)
     }
 }
 
+// 2D: a CTA owns the rows [y0, y0+yn) of a chunk and marches along y through the same
+// two levels on whole rows (x neighbours by shuffle, the periodic wrap by lanes 0/31):
+//   level 1 (step n)   on rows y0-1 .. y0+yn, from level-0 rows y0-2 .. y0+yn+1 that the
+//                       TMA engine stages in a ring of kT2Slots rows, kT2Ahead rows ahead;
+//   level 2 (step n+1) on rows y0 .. y0+yn-1, from level-1 rows kept in a second 4-slot
+//                       ring, two rows behind level 1, so each row needs one barrier.
+// y is the marching direction, so the only recomputed level-1 rows are the two outside
+// the chunk.  As in 3D, dphi enters those rows from the neighbouring chunks, so it is
+// read from one buffer and written to another; it is loaded two rows ahead.
+constexpr int kTb2Threads = 512;
+constexpr int kT2Ahead = 3;             // level-0 rows in flight
+constexpr int kT2Slots = kT2Ahead + 3;  // a row is read by level 1 over three iterations
+
+static __device__ __noinline__ void drain_rows(uint64_t* bar, int from, int issued, unsigned int* err)
+{
+    for (int i = from; i <= issued; ++i) mbar_wait(&bar[i % kT2Slots], (i / kT2Slots) & 1, err);
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kTb2Threads, 1)
+    k_step2d_t2(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
+                float* __restrict__ v_out, int nx, int ny, int cy, StepCoef<float> k0, StepCoef<float> k1,
+                RunConst<float> rc, unsigned int* err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* ring0 = reinterpret_cast<float*>(smem_raw + 128);
+    float* ring1 = ring0 + kT2Slots * nx;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int y0 = blockIdx.x * cy;
+    const int yn = min(cy, ny - y0);
+    const int nq = nx >> 2;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < kT2Slots; ++i) mbar_init(&bar[i], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto wy = [&](int y) {  // periodic; a chunk's outside rows wrap at most twice around a small box
+        while (y < 0) y += ny;
+        while (y >= ny) y -= ny;
+        return y;
+    };
+    const unsigned rowb = (unsigned)nx * 4u;
+    const int nload = yn + 4;  // level-0 local rows 0..yn+3 = global y0-2 .. y0+yn+1
+    auto issue = [&](int i) {
+        uint64_t* b = &bar[i % kT2Slots];
+        mbar_arrive_expect_tx(b, rowb);
+        bulk_g2s(ring0 + (i % kT2Slots) * nx, phi_in + (size_t)wy(y0 - 2 + i) * nx, rowb, b);
+    };
+    int issued = -1;
+    if (tid == 0)
+        for (int i = 0; i < kT2Ahead && i < nload; ++i) issue(i), issued = i;
+
+    int col[ITEMS];
+    bool on[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int q = tid + kTb2Threads * j;
+        on[j] = q < nq;  // whole warps: nq and the block size are multiples of 32
+        col[j] = on[j] ? q : 0;
+    }
+    // dphi^{n-1/2} of level-1 rows j1 (used now), j1+1 and j1+2 (loaded ahead)
+    float4 va[ITEMS], vb[ITEMS], vc[ITEMS];
+    // level-1 dphi^{n+1/2} of this thread's sites for the last three level-1 rows
+    float4 w0[ITEMS], w1[ITEMS], w2[ITEMS];
+    auto load_v = [&](int jl, float4* dst) {  // level-0 local row jl
+        const float* vp = v_in + (size_t)wy(y0 - 2 + jl) * nx;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j)
+            if (on[j]) dst[j] = ldg_stream4(vp + 4 * col[j]);
+    };
+
+    for (int i = 0; i <= yn + 4; ++i) {
+        bool ok = true;
+        if (i < nload) ok = mbar_wait(&bar[i % kT2Slots], (i / kT2Slots) & 1, err);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) drain_rows(bar, i, issued, err);
+            return;
+        }
+        // into the slot of row i+kT2Ahead-kT2Slots = i-3, last read by level 1 at iteration i-1
+        if (tid == 0 && i + kT2Ahead < nload) issue(i + kT2Ahead), issued = i + kT2Ahead;
+        const int j1 = i - 1;  // level-1 row of this iteration
+        const int k2 = i - 3;  // level-2 row of this iteration
+        const bool next_v = i + 1 >= 1 && i + 1 <= yn + 2;  // dphi of level-1 row i+1, two iterations ahead
+        if (next_v) load_v(i + 1, vc);
+        if (j1 >= 1 && j1 <= yn + 2) {
+            const float* pm = ring0 + ((j1 - 1) % kT2Slots) * nx;
+            const float* pc = ring0 + (j1 % kT2Slots) * nx;
+            const float* pp = ring0 + ((j1 + 1) % kT2Slots) * nx;
+            float* l1 = ring1 + (j1 & 3) * nx;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if (!on[j]) continue;
+                const float4 c = lds4(pc + 4 * col[j]);
+                float left, right;
+                x_halo(pc, col[j], nq, nx, lane, c, left, right);
+                const float4 ym = lds4(pm + 4 * col[j]);
+                float4 pn;
+                float4 vv = va[j];
+                update4(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, k0, rc, false);
+                *reinterpret_cast<float4*>(l1 + 4 * col[j]) = pn;
+                w2[j] = vv;
+            }
+        }
+        if (k2 >= 2 && k2 <= yn + 1) {
+            const float* pm = ring1 + ((k2 - 1) & 3) * nx;
+            const float* pc = ring1 + (k2 & 3) * nx;
+            const float* pp = ring1 + ((k2 + 1) & 3) * nx;
+            const size_t ro = (size_t)(y0 - 2 + k2) * nx;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if (!on[j]) continue;
+                const float4 c = lds4(pc + 4 * col[j]);
+                float left, right;
+                x_halo(pc, col[j], nq, nx, lane, c, left, right);
+                const float4 ym = lds4(pm + 4 * col[j]);
+                float4 pn;
+                float4 vv = w0[j];
+                update4(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, k1, rc, false);
+                stg4(phi_out + ro + 4 * col[j], pn);
+                stg4(v_out + ro + 4 * col[j], vv);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            w0[j] = w1[j];
+            w1[j] = w2[j];
+            va[j] = vb[j];
+            vb[j] = vc[j];
+        }
+    }
+}
+
 size_t smem_t2(int nx, int ty) { return 128 + 4 * (size_t)(ty + 4) * nx * 4 + 4 * (size_t)(ty + 2) * nx * 4; }
 
 constexpr size_t kTbSmemMax = 200 * 1024;
@@ -172,15 +308,42 @@ int pick_ty(const Geo& g)
 
 }  // namespace
 
+size_t smem2d_t2(int nx) { return 128 + (kT2Slots + 4) * (size_t)nx * sizeof(float); }
+
 bool tblock_ok(const Geo& g, int precision)
 {
-    return precision == PRS_FP32 && g.dims == 3 && g.nx % 128 == 0 && g.nx <= 1024 && g.nz >= 3 && pick_ty(g) > 0;
+    if (precision != PRS_FP32 || g.nx % 128 != 0) return false;
+    if (g.dims == 2) return g.nx <= 2 * kTb2Threads * 4;  // at most two float4 per thread of a row
+    return g.nx <= 1024 && g.nz >= 3 && pick_ty(g) > 0;
 }
 
 cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
                            StepCoef<float> k0, StepCoef<float> k1, RunConst<float> rc, unsigned int* err,
                            cudaStream_t st)
 {
+    if (g.dims == 2) {
+        static std::atomic<unsigned long long> attr1{0}, attr2{0};
+        const size_t sm = smem2d_t2(g.nx);
+        const int sms = sm_count_current();
+        // one CTA per SM (the two rings take 10 rows); chunks of rows for one full wave
+        const int cy = (g.ny + sms - 1) / sms;
+        const int blocks = (g.ny + cy - 1) / cy;
+        // the shared-memory limit is set once per device, to the largest row each variant takes
+        if (g.nx / 4 > kTb2Threads) {
+            const cudaError_t e =
+                smem_limit_once(attr2, (const void*)k_step2d_t2<2>, (int)smem2d_t2(8 * kTb2Threads));
+            if (e != cudaSuccess) return e;
+            k_step2d_t2<2><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
+                                                            rc, err);
+        } else {
+            const cudaError_t e =
+                smem_limit_once(attr1, (const void*)k_step2d_t2<1>, (int)smem2d_t2(4 * kTb2Threads));
+            if (e != cudaSuccess) return e;
+            k_step2d_t2<1><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
+                                                            rc, err);
+        }
+        return cudaGetLastError();
+    }
     static std::atomic<unsigned long long> attr{0};
     {
         const cudaError_t e = smem_limit_once(attr, (const void*)k_step3d_t2<kTbItems>, (int)kTbSmemMax);

@@ -131,7 +131,8 @@ def test_fp32_close(shape, era_m):
 @pytest.mark.parametrize("nsteps", [23, 8, 2, 1])
 @pytest.mark.parametrize("tblock", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(256, 256), (64, 48, 40), (128, 64, 40), (256, 32, 24), (512, 16, 12),
-                                   (1024, 8, 10), (128, 32, 3), (256, 48, 7)])
+                                   (1024, 8, 10), (128, 32, 3), (256, 48, 7),
+                                   (512, 96), (4096, 12), (1024, 5), (2048, 40), (128, 3)])
 def test_fp32_temporal_blocks(shape, tblock, nsteps):
     """Every fused-steps-per-pass setting (and the mix of one- and two-step passes it implies)
     gives the oracle's field to FP32 rounding; dphi always ends in the run's own buffer."""
@@ -335,9 +336,18 @@ def test_full_size_3d_1024_sampled(tblock):
     assert worst <= 1e-5  # |phi| < 1.1: absolute ~ relative
 
 
-def test_full_size_2d_4096_sampled():
-    worst = _sampled_step_check((4096, 4096), 6, 0)
+@pytest.mark.parametrize("tblock", [0, 2])
+def test_full_size_2d_4096_sampled(tblock):
+    """2D 4096^2 FP32 (0: the library default; 2: two-step passes): sampled sites after 6 steps."""
+    worst = _sampled_step_check((4096, 4096), 6, tblock)
     assert worst <= 1e-5
+
+
+def test_two_step_passes_match_single_steps_2d():
+    shape = (4096, 64)
+    a = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=1)
+    b = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=2)
+    assert _rel(b[0], a[0].astype(np.float64)) <= 1e-5 and _rel(b[1], a[1].astype(np.float64)) <= 1e-5
 
 
 def _fill(sim, phi_profile, v_profile, axis_len_last=True):
