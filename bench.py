@@ -277,7 +277,9 @@ def run_gpu(args, world, rank, local):
     # fused into its first leapfrog step (prs_step_measure), then the other interval-1
     # steps (prs_step); events bracket the two calls separately
     rest = args.interval - 1
-    pairs = (rest // 2) & ~1 if tb == 2 else 0
+    pairs = rest // 2 if tb == 2 else 0  # the library's split of prs_step(rest) into passes
+    if pairs % 2 and rest == 2 * pairs:
+        pairs -= 1
     singles = rest - 2 * pairs
     step_launches = pairs + singles
 

@@ -353,11 +353,13 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
     int tb = s->p.tblock > 0 ? s->p.tblock : default_fused_steps(s->g, s->p.precision, repro);
     if (tb > tmax) tb = tmax;
     if (tb < 1) tb = 1;
-    // Two-step passes read dphi across sites, so they write it to a second buffer;
-    // an even number of them leaves dphi where it started.  The remaining steps
-    // are single-step passes, which update dphi in place.
+    // Two-step passes read dphi across sites, so they write it to a second buffer.
+    // After an odd number of them dphi sits in that buffer: the single step after
+    // them reads it there and writes the run's own buffer, so an odd step count keeps
+    // every pair; with an even count and an odd number of pairs, one pair runs as two
+    // single steps instead.  Single steps otherwise update dphi in place.
     int64_t pairs = tb == 2 ? nsteps / 2 : 0;
-    if (pairs & 1) --pairs;
+    if ((pairs & 1) && nsteps == 2 * pairs) --pairs;
     if (pairs > 0 && !s->dphi_alt) {
         if (cudaMalloc(&s->dphi_alt, (size_t)s->g.S * s->elem) != cudaSuccess) {
             cudaGetLastError();
@@ -367,26 +369,27 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
     }
     const int64_t singles = nsteps - 2 * pairs;
     unsigned int* err = &s->d_status->error;
-    for (int64_t k = 0; k < singles; ++k) {
-        double c[5];
-        step_coefficients(s->p, s->n + k, c);
-        cudaError_t e = launch_step(s->g, s->p.precision, repro, s->phi[s->cur], s->phi[1 - s->cur], s->dphi, &c[0],
-                                    &c[1], &c[2], 1, s->rc, err, s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
-        s->cur = 1 - s->cur;
-    }
     const RunConst<float> rcf{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
                               (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
     void* vbuf[2] = {s->dphi, s->dphi_alt};
     for (int64_t k = 0; k < pairs; ++k) {
         double a[5], b[5];
-        const int64_t n = s->n + singles + 2 * k;
+        const int64_t n = s->n + 2 * k;
         step_coefficients(s->p, n, a);
         step_coefficients(s->p, n + 1, b);
         cudaError_t e = launch_step_t2(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
                                        (const float*)vbuf[k & 1], (float*)vbuf[1 - (k & 1)],
                                        StepCoef<float>{(float)a[0], (float)a[1], (float)a[2]},
                                        StepCoef<float>{(float)b[0], (float)b[1], (float)b[2]}, rcf, err, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
+        s->cur = 1 - s->cur;
+    }
+    for (int64_t k = 0; k < singles; ++k) {
+        double c[5];
+        step_coefficients(s->p, s->n + 2 * pairs + k, c);
+        const void* v_in = (k == 0 && (pairs & 1)) ? s->dphi_alt : s->dphi;  // brings dphi home
+        cudaError_t e = launch_step_io(s->g, s->p.precision, repro, s->phi[s->cur], s->phi[1 - s->cur], v_in,
+                                       s->dphi, &c[0], &c[1], &c[2], 1, s->rc, err, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
         s->cur = 1 - s->cur;
     }

@@ -128,7 +128,7 @@ def test_fp32_close(shape, era_m):
     assert _rel(v, ov) <= 1e-5
 
 
-@pytest.mark.parametrize("nsteps", [23, 8, 2, 1])
+@pytest.mark.parametrize("nsteps", [23, 8, 6, 3, 2, 1])
 @pytest.mark.parametrize("tblock", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(256, 256), (64, 48, 40), (128, 64, 40), (256, 32, 24), (512, 16, 12),
                                    (1024, 8, 10), (128, 32, 3), (256, 48, 7),
