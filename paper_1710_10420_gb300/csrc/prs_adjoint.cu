@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
     const int yn = min(T.len, ny - y0);
     const int nb = yn / rb;
     const int nq = nx >> 2;
-    const int ringrows = 4 * rb;
+    const int rmask = 4 * rb - 1;  // ring rows: a power of two (rb = 2048/nx, nx dividing 2048)
     const unsigned rowb = (unsigned)nx * 4u;
     if (tid == 0) {
 #pragma unroll
@@ -476,8 +476,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int lr = (bi + 1) * rb + row[j];
-            const int rc0 = (lr % ringrows) * nx, ru = ((lr + ringrows - 1) % ringrows) * nx,
-                      rd = ((lr + 1) % ringrows) * nx;
+            const int rc0 = (lr & rmask) * nx, ru = ((lr - 1) & rmask) * nx, rd = ((lr + 1) & rmask) * nx;
             const float4 c = lds4(ringL + rc0 + 4 * col[j]);
             float left, right;
             x_halo(ringL + rc0, col[j], nq, nx, lane, c, left, right);

@@ -428,7 +428,8 @@ __device__ __forceinline__ bool tile2d(const Tile2D& T, const StepCoef<float>& k
     const int nq = nx >> 2;
     const double rscale = MEAS && rc.V0 > 0.0f ? 1.0 / (double)rc.V0 : 0.0;  // see wall_sites4
     const int slot = rb * nx;
-    const int ringrows = 4 * rb;
+    const int ringrows = 4 * rb;  // a power of two: rb = 4096/nx rows, nx a multiple of 128 dividing 4096
+    const int rmask = ringrows - 1;
     const unsigned rowb = (unsigned)nx * 4u;
 
     if (tid == 0) {
@@ -498,16 +499,16 @@ __device__ __forceinline__ bool tile2d(const Tile2D& T, const StepCoef<float>& k
             for (int i = 1; i < ITEMS; ++i)
                 if (jj == i) r = row[i], cb = col[i];
             const int lr = (bi + 1) * rb + r;
-            a.pw += weight2(ring + (size_t)((lr + ringrows - 1) % ringrows) * nx, ring + (size_t)(lr % ringrows) * nx,
-                            ring + (size_t)((lr + 1) % ringrows) * nx, 4 * (cb - lane + (int)((ent >> 4) & 31)) + e, d,
+            a.pw += weight2(ring + (size_t)((lr - 1) & rmask) * nx, ring + (size_t)(lr & rmask) * nx,
+                            ring + (size_t)((lr + 1) & rmask) * nx, 4 * (cb - lane + (int)((ent >> 4) & 31)) + e, d,
                             nx);
         };
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int lr = (bi + 1) * rb + row[j];  // local row of this site in ring order
-            const float* crow = ring + (size_t)(lr % ringrows) * nx;
-            const float* urow = ring + (size_t)((lr + ringrows - 1) % ringrows) * nx;
-            const float* drow = ring + (size_t)((lr + 1) % ringrows) * nx;
+            const float* crow = ring + (size_t)(lr & rmask) * nx;
+            const float* urow = ring + (size_t)((lr - 1) & rmask) * nx;
+            const float* drow = ring + (size_t)((lr + 1) & rmask) * nx;
             float4 c = lds4(crow + 4 * col[j]);
             float4 ym = lds4(urow + 4 * col[j]);
             float4 yp = lds4(drow + 4 * col[j]);
