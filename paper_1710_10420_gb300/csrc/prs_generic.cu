@@ -142,6 +142,18 @@ cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const v
     return step_generic_t<double, false>(g, in, out, dphi, dphi_out, c1, c2, cV, rcd, st);
 }
 
+// Grid of the row-wise kernels: up to four x blocks per row, y blocks striding over the
+// rows, at most cap blocks in all.
+static dim3 rows_grid(const Geo& g, int cap)
+{
+    const int gx = (g.nx + 255) / 256 < 4 ? (g.nx + 255) / 256 : 4;
+    int64_t gy = cap / gx;
+    const int64_t rows = (int64_t)g.ny * g.nz;
+    if (gy > rows) gy = rows;
+    if (gy < 1) gy = 1;
+    return dim3((unsigned)gx, (unsigned)gy, 1);
+}
+
 // ------------------------------------------------------------ diagnostics
 
 template <typename R>
@@ -206,43 +218,44 @@ __global__ void __launch_bounds__(256) k_measure(const R* __restrict__ phi, cons
 {
     using A = Arith<R, true>;
     DiagAcc a{0.0, 0.0, 0, 0, 0, 0};
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.S; s += (int64_t)gridDim.x * blockDim.x) {
-        int64_t x = s % g.nx;
-        int64_t r = s / g.nx;
-        int64_t y = r % g.ny;
-        int64_t z = r / g.ny;
-        R ps = phi[s];
-        R vs = dphi[s];
-        bool neg = ps < (R)0;
-        if (!isfinite(ps) || !isfinite(vs)) a.n_nonfinite++;
-        bool wall = false;
+    const int64_t rows = (int64_t)g.ny * g.nz;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int64_t y = row % g.ny, z = row / g.ny;  // once per row
+        for (int64_t x = blockIdx.x * blockDim.x + threadIdx.x; x < g.nx; x += gridDim.x * blockDim.x) {
+            const int64_t s = row * g.nx + x;
+            R ps = phi[s];
+            R vs = dphi[s];
+            bool neg = ps < (R)0;
+            if (!isfinite(ps) || !isfinite(vs)) a.n_nonfinite++;
+            bool wall = false;
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            int ex = (d == 0), ey = (d == 1), ez = (d == 2);
-            R pt = fetch(phi, g, x + ex, y + ey, z + ez);
-            R pm = fetch(phi, g, x - ex, y - ey, z - ez);
-            if ((pt < (R)0) != neg) {
-                a.n_links++;
-                a.sum_w += (double)link_weight<R, D>(phi, g, x, y, z, d, ps, pt);
-                wall = true;
+            for (int d = 0; d < D; ++d) {
+                int ex = (d == 0), ey = (d == 1), ez = (d == 2);
+                R pt = fetch(phi, g, x + ex, y + ey, z + ez);
+                R pm = fetch(phi, g, x - ex, y - ey, z - ez);
+                if ((pt < (R)0) != neg) {
+                    a.n_links++;
+                    a.sum_w += (double)link_weight<R, D>(phi, g, x, y, z, d, ps, pt);
+                    wall = true;
+                }
+                if ((pm < (R)0) != neg) wall = true;
             }
-            if ((pm < (R)0) != neg) wall = true;
-        }
-        if (wall) {
-            a.n_wall++;
-            // u = phi^2/phi0^2 - 1.  FP64 keeps the order of Eq. 1; FP32 factors it as
-            // (phi - phi0)(phi + phi0)/phi0^2, equal in exact arithmetic and free of
-            // the cancellation of phi^2 - 1 next to the vacua.
-            R u;
-            if (sizeof(R) == 8)
-                u = A::sub(A::mul(A::mul(ps, ps), rc.inv_phi0sq), (R)1);
-            else
-                u = A::mul(A::mul(A::sub(ps, rc.phi0), A::add(ps, rc.phi0)), rc.inv_phi0sq);
-            R V = A::mul(A::mul(rc.V0, u), u);
-            if (V > (R)0)
-                a.sum_ratio += (double)A::div(A::mul(vs, vs), V);
-            else
-                a.n_vzero++;
+            if (wall) {
+                a.n_wall++;
+                // u = phi^2/phi0^2 - 1.  FP64 keeps the order of Eq. 1; FP32 factors it as
+                // (phi - phi0)(phi + phi0)/phi0^2, equal in exact arithmetic and free of
+                // the cancellation of phi^2 - 1 next to the vacua.
+                R u;
+                if (sizeof(R) == 8)
+                    u = A::sub(A::mul(A::mul(ps, ps), rc.inv_phi0sq), (R)1);
+                else
+                    u = A::mul(A::mul(A::sub(ps, rc.phi0), A::add(ps, rc.phi0)), rc.inv_phi0sq);
+                R V = A::mul(A::mul(rc.V0, u), u);
+                if (V > (R)0)
+                    a.sum_ratio += (double)A::div(A::mul(vs, vs), V);
+                else
+                    a.n_vzero++;
+            }
         }
     }
     block_reduce_and_finish(a, scr);
@@ -252,14 +265,12 @@ template <typename R>
 static cudaError_t measure_t(const Geo& g, const void* phi, const void* dphi, const double rcd[6],
                              const DiagScratch& scr, cudaStream_t st)
 {
-    const int block = 256;
-    int grid = grid_for(g.S, block);
-    if (grid > scr.max_blocks) grid = scr.max_blocks;
+    const dim3 grid = rows_grid(g, scr.max_blocks < 152 * 8 ? scr.max_blocks : 152 * 8);  // one partial per block
     RunConst<R> rc = make_rc<R>(rcd);
     if (g.dims == 3)
-        k_measure<R, 3><<<grid, block, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
+        k_measure<R, 3><<<grid, 256, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
     else
-        k_measure<R, 2><<<grid, block, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
+        k_measure<R, 2><<<grid, 256, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
     return cudaGetLastError();
 }
 
@@ -280,10 +291,11 @@ static cudaError_t measure_grid_t(const Geo& g, const void* phi, const void* dph
                                   const DiagScratch& scr, int grid, cudaStream_t st)
 {
     RunConst<R> rc = make_rc<R>(rcd);
+    const dim3 g2(1, (unsigned)grid, 1);  // grid blocks striding over the rows
     if (g.dims == 3)
-        k_measure<R, 3><<<grid, 256, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
+        k_measure<R, 3><<<g2, 256, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
     else
-        k_measure<R, 2><<<grid, 256, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
+        k_measure<R, 2><<<g2, 256, 0, st>>>((const R*)phi, (const R*)dphi, g, rc, scr);
     return cudaGetLastError();
 }
 
