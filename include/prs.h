@@ -101,9 +101,11 @@ typedef struct {
     double phi0;       /* vacuum value (> 0)                                        */
     uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
     uint32_t flags;    /* PRS_REPRO | PRS_FP32_CR | PRS_DEBUG, or 0                 */
-    int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (1);
-                          2 = two-step passes for FP32 3D boxes with an x side that is a
-                          multiple of 128 up to 1024 (else 1); at most 8            */
+    int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (2 for
+                          FP32 2D boxes of at least 2^24 sites, else 1, see
+                          prs_default_tblock); 2 = two-step passes for FP32 boxes with an
+                          x side that is a multiple of 128 up to 1024 (3D) or 4096 (2D),
+                          else 1; at most 8 (values above 2 act as 2)               */
 } prs_params;
 
 /* One output record of the wall diagnostics (Eq. 7, Eq. 8). */
