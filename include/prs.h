@@ -146,7 +146,11 @@ int prs_bind(prs_sim* sim, void* d_phi_a, void* d_phi_b, void* d_dphi);
 int prs_init(prs_sim* sim, const void* h_phi, const void* h_dphi);
 
 /* Queue nsteps (>= 0) leapfrog steps (Eqs. 3-6) on the run's stream; returns
- * without waiting.  Step n uses delta_n, eta_n = eta0 + n deta. */
+ * without waiting.  Step n uses delta_n, eta_n = eta0 + n deta.  Passes of two
+ * steps (see prs_params.tblock) write dphi out of place: the first call that makes
+ * them allocates a second dphi buffer, owned by the run and freed by prs_destroy (if
+ * that allocation fails, the steps run one per pass).  dphi always ends in the run's
+ * own buffer. */
 int prs_step(prs_sim* sim, int64_t nsteps);
 
 /* Wall diagnostics of the current state (Eq. 7, Eq. 8), reduced on the device in
