@@ -37,6 +37,7 @@ WORKLOADS = {
 }
 BYTES_PER_SITE_UPDATE = {0: 16, 1: 32}  # read+write of phi and dphi (FP32, FP64)
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
 def parse():
@@ -331,6 +332,7 @@ def run_gpu(args, world, rank, local):
                 "note": "achieved = 16 B x site-updates of one launch / its mean duration; with two steps per "
                         "pass this effective figure can exceed the copy bandwidth, dram_frac is the measured one",
                 "launch_ms": launch_avg_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                 "fused_step_and_diagnostics_ms": fused_ms}
     if rec:
         roofline["dram_frac"] = rec["dram_bytes_per_launch"] / (launch_avg_ms / 1e3) / 1e9 / peak
