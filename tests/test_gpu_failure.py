@@ -74,11 +74,11 @@ def test_stability_limit_checked_at_every_call():
 
 # ------------------------------------------------------------------ PRS_DEBUG
 
-def _raw_run(shape, flags, precision=prs.PRS_FP32, seed=5):
+def _raw_run(shape, flags, precision=prs.PRS_FP32, seed=5, tblock=0):
     """A run on library-owned buffers (prs_create + prs_init), as a C caller makes one."""
     import torch
 
-    h = prs.prs_create(prs.make_params(shape, precision=precision, seed=seed, flags=flags),
+    h = prs.prs_create(prs.make_params(shape, precision=precision, seed=seed, flags=flags, tblock=tblock),
                        torch.cuda.current_stream().cuda_stream)
     prs.prs_init(h)
     return h
@@ -149,3 +149,24 @@ def test_debug_reports_a_nonfinite_state():
         finally:
             prs.prs_destroy(h)
     _still_works()
+
+
+@pytest.mark.parametrize("shape", [(4096, 40), (512, 96), (256, 64, 24), (128, 32, 8)])
+def test_debug_two_step_passes_stay_in_bounds(shape):
+    """Two-step passes (2D and 3D) under PRS_DEBUG: the guard bands around the fields stay
+    intact and the state matches one step per pass to FP32 rounding (7 steps: three pairs,
+    then the single step that brings dphi back to the run's buffer)."""
+    out = []
+    for flags, tb in ((prs.PRS_DEBUG, 2), (0, 1)):
+        h = _raw_run(shape, flags, tblock=tb)
+        try:
+            assert prs.load().prs_step(h, 7) == prs.PRS_OK, prs.prs_last_error()
+            phi = np.empty(tuple(reversed(shape)), np.float32)
+            v = np.empty_like(phi)
+            prs.prs_get_state(h, phi, v)
+        finally:
+            prs.prs_destroy(h)
+        out.append((phi, v))
+    (pa, va), (pb, vb) = out
+    assert np.max(np.abs(pa - pb)) <= 1e-5 * np.max(np.abs(pb))
+    assert np.max(np.abs(va - vb)) <= 1e-5 * np.max(np.abs(vb))
