@@ -667,14 +667,17 @@ def scaling_exponents(series, ln_eta_min: float = 2.58) -> dict:
             "mu_runs": [float(x) for x in mus], "nu_runs": [float(x) for x in nus]}
 
 
-def run_table1_figure(prs, stream, dev, seeds=(1, 2, 3, 4, 5)) -> dict:
+TABLE1_BOXES = {"2048^2": (2048, 2048), "128^3": (128, 128, 128)}
+
+
+def run_table1_figure(prs, stream, dev, seeds=(1, 2, 3, 4, 5), boxes=None) -> dict:
     """Scaling exponents of A/V and gamma v (Eq. 9) from five radiation-era runs of 2D 2048^2 to
     eta = 1024 and 3D 128^3 to eta = 64, outputs every 10 steps (every unit of eta).  FP32 runs go
     through the ensemble engine, FP64 runs through prs_step + prs_measure; both start from the
     same seeded field (exactly representable in FP32)."""
     import torch
 
-    boxes = {"2048^2": (2048, 2048), "128^3": (128, 128, 128)}
+    boxes = boxes or TABLE1_BOXES
     every = 10
     t0 = time.perf_counter()
     runs = [(name, shape, sd) for name, shape in boxes.items() for sd in seeds]
@@ -706,7 +709,7 @@ def run_table1_figure(prs, stream, dev, seeds=(1, 2, 3, 4, 5)) -> dict:
             rows = np.array(rows)
             series[(name, "fp64")].append((rows[:, 0], rows[:, 1], rows[:, 2]))
     t_fp64 = time.perf_counter() - t0
-    table = {name: {prec: dict(scaling_exponents(series[(name, prec)]), paper=TABLE1_PAPER[name][prec])
+    table = {name: {prec: dict(scaling_exponents(series[(name, prec)]), paper=TABLE1_PAPER.get(name, {}).get(prec))
                     for prec in ("fp32", "fp64")} for name in boxes}
     # from white noise the 3D walls start almost at rest: gamma v falls to ~0.08 by eta ~ 15 and
     # climbs back to ~0.5 by eta ~ 27, inside the paper's fit range; the same fit past eta = 27
