@@ -156,31 +156,35 @@ __global__ void __launch_bounds__(kTbThreads, 1)
 // 2D: a CTA owns the rows [y0, y0+yn) of a chunk and marches along y through the same
 // two levels on whole rows (x neighbours by shuffle, the periodic wrap by lanes 0/31):
 //   level 1 (step n)   on rows y0-1 .. y0+yn, from level-0 rows y0-2 .. y0+yn+1 that the
-//                       TMA engine stages in a ring of kT2Slots rows, kT2Ahead rows ahead;
-//   level 2 (step n+1) on rows y0 .. y0+yn-1, from level-1 rows kept in a second 4-slot
-//                       ring, two rows behind level 1, so each row needs one barrier.
+//                       TMA engine stages in a ring of kR2Slots0 rows;
+//   level 2 (step n+1) on rows y0 .. y0+yn-1, from level-1 rows kept in a ring of
+//                       kR2Slots1 rows.
+// Iteration t runs level 1 on local rows 2t-1, 2t and level 2 on rows 2t-4, 2t-3, whose
+// level-1 rows (up to 2t-2) were written an iteration earlier: one barrier per two rows.
 // y is the marching direction, so the only recomputed level-1 rows are the two outside
-// the chunk.  As in 3D, dphi enters those rows from the neighbouring chunks, so it is
-// read from one buffer and written to another; it is loaded two rows ahead.
+// the chunk.  As in 3D, dphi enters those rows from the neighbouring chunks, so it is read
+// from one buffer and written to another; the level-1 dphi stays in the registers of the
+// thread that owns its columns.
 constexpr int kTb2Threads = 512;
-constexpr int kT2Ahead = 3;             // level-0 rows in flight
-constexpr int kT2Slots = kT2Ahead + 3;  // a row is read by level 1 over three iterations
+constexpr int kR2Ahead = 1;                   // iterations of level-0 rows in flight
+constexpr int kR2Slots0 = 4 + 2 * kR2Ahead;  // level-0 ring rows
+constexpr int kR2Slots1 = 6;                 // level-1 ring rows
 
 static __device__ __noinline__ void drain_rows(uint64_t* bar, int from, int issued, unsigned int* err)
 {
-    for (int i = from; i <= issued; ++i) mbar_wait(&bar[i % kT2Slots], (i / kT2Slots) & 1, err);
+    for (int i = from; i <= issued; ++i) mbar_wait(&bar[i % kR2Slots0], (i / kR2Slots0) & 1, err);
 }
 
 template <int ITEMS>
 __global__ void __launch_bounds__(kTb2Threads, 1)
     k_step2d_t2(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
-                float* __restrict__ v_out, int nx, int ny, int cy, StepCoef<float> k0, StepCoef<float> k1,
-                RunConst<float> rc, unsigned int* err)
+                  float* __restrict__ v_out, int nx, int ny, int cy, StepCoef<float> k0, StepCoef<float> k1,
+                  RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* ring0 = reinterpret_cast<float*>(smem_raw + 128);
-    float* ring1 = ring0 + kT2Slots * nx;
+    float* ring1 = ring0 + kR2Slots0 * nx;
     const int tid = threadIdx.x, lane = tid & 31;
     const int y0 = blockIdx.x * cy;
     const int yn = min(cy, ny - y0);
@@ -188,106 +192,121 @@ __global__ void __launch_bounds__(kTb2Threads, 1)
 
     if (tid == 0) {
 #pragma unroll
-        for (int i = 0; i < kT2Slots; ++i) mbar_init(&bar[i], 1);
+        for (int i = 0; i < kR2Slots0; ++i) mbar_init(&bar[i], 1);
         mbar_fence_init();
     }
     __syncthreads();
 
-    auto wy = [&](int y) {  // periodic; a chunk's outside rows wrap at most twice around a small box
+    auto wy = [&](int y) {
         while (y < 0) y += ny;
         while (y >= ny) y -= ny;
         return y;
     };
     const unsigned rowb = (unsigned)nx * 4u;
     const int nload = yn + 4;  // level-0 local rows 0..yn+3 = global y0-2 .. y0+yn+1
-    auto issue = [&](int i) {
-        uint64_t* b = &bar[i % kT2Slots];
+    auto issue = [&](int i) {  // level-0 local row i
+        uint64_t* b = &bar[i % kR2Slots0];
         mbar_arrive_expect_tx(b, rowb);
-        bulk_g2s(ring0 + (i % kT2Slots) * nx, phi_in + (size_t)wy(y0 - 2 + i) * nx, rowb, b);
+        bulk_g2s(ring0 + (i % kR2Slots0) * nx, phi_in + (size_t)wy(y0 - 2 + i) * nx, rowb, b);
     };
+    // iteration t waits for rows 2t, 2t+1 and issues the two rows iteration t + kR2Ahead waits for
     int issued = -1;
     if (tid == 0)
-        for (int i = 0; i < kT2Ahead && i < nload; ++i) issue(i), issued = i;
+        for (int i = 0; i < 2 * kR2Ahead && i < nload; ++i) issue(i), issued = i;
 
     int col[ITEMS];
     bool on[ITEMS];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int q = tid + kTb2Threads * j;
-        on[j] = q < nq;  // whole warps: nq and the block size are multiples of 32
+        on[j] = q < nq;
         col[j] = on[j] ? q : 0;
     }
-    // dphi^{n-1/2} of level-1 rows j1 (used now), j1+1 and j1+2 (loaded ahead)
-    float4 va[ITEMS], vb[ITEMS], vc[ITEMS];
-    // level-1 dphi^{n+1/2} of this thread's sites for the last three level-1 rows
-    float4 w0[ITEMS], w1[ITEMS], w2[ITEMS];
-    auto load_v = [&](int jl, float4* dst) {  // level-0 local row jl
+    // dphi^{n-1/2} of level-1 rows 2t-1, 2t (a: now, b: loaded for the next iteration)
+    float4 va0[ITEMS], va1[ITEMS], vb0[ITEMS], vb1[ITEMS];
+    // level-1 dphi^{n+1/2}: even rows for two iterations, odd rows for one
+    float4 e0[ITEMS], e1[ITEMS], o0[ITEMS];
+    auto load_v = [&](int jl, float4* dst) {
+        if (jl < 1 || jl > yn + 2) return;
         const float* vp = v_in + (size_t)wy(y0 - 2 + jl) * nx;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j)
             if (on[j]) dst[j] = ldg_stream4(vp + 4 * col[j]);
     };
 
-    for (int i = 0; i <= yn + 4; ++i) {
-        bool ok = true;
-        if (i < nload) ok = mbar_wait(&bar[i % kT2Slots], (i / kT2Slots) & 1, err);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) drain_rows(bar, i, issued, err);
-            return;
-        }
-        // into the slot of row i+kT2Ahead-kT2Slots = i-3, last read by level 1 at iteration i-1
-        if (tid == 0 && i + kT2Ahead < nload) issue(i + kT2Ahead), issued = i + kT2Ahead;
-        const int j1 = i - 1;  // level-1 row of this iteration
-        const int k2 = i - 3;  // level-2 row of this iteration
-        const bool next_v = i + 1 >= 1 && i + 1 <= yn + 2;  // dphi of level-1 row i+1, two iterations ahead
-        if (next_v) load_v(i + 1, vc);
-        if (j1 >= 1 && j1 <= yn + 2) {
-            const float* pm = ring0 + ((j1 - 1) % kT2Slots) * nx;
-            const float* pc = ring0 + (j1 % kT2Slots) * nx;
-            const float* pp = ring0 + ((j1 + 1) % kT2Slots) * nx;
-            float* l1 = ring1 + (j1 & 3) * nx;
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                if (!on[j]) continue;
-                const float4 c = lds4(pc + 4 * col[j]);
-                float left, right;
-                x_halo(pc, col[j], nq, nx, lane, c, left, right);
-                const float4 ym = lds4(pm + 4 * col[j]);
-                float4 pn;
-                float4 vv = va[j];
-                update4(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, k0, rc, false);
-                *reinterpret_cast<float4*>(l1 + 4 * col[j]) = pn;
-                w2[j] = vv;
-            }
-        }
-        if (k2 >= 2 && k2 <= yn + 1) {
-            const float* pm = ring1 + ((k2 - 1) & 3) * nx;
-            const float* pc = ring1 + (k2 & 3) * nx;
-            const float* pp = ring1 + ((k2 + 1) & 3) * nx;
-            const size_t ro = (size_t)(y0 - 2 + k2) * nx;
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                if (!on[j]) continue;
-                const float4 c = lds4(pc + 4 * col[j]);
-                float left, right;
-                x_halo(pc, col[j], nq, nx, lane, c, left, right);
-                const float4 ym = lds4(pm + 4 * col[j]);
-                float4 pn;
-                float4 vv = w0[j];
-                update4(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, k1, rc, false);
-                stg4(phi_out + ro + 4 * col[j], pn);
-                stg4(v_out + ro + 4 * col[j], vv);
-            }
-        }
+    auto level1 = [&](int jr, const float4* vin, float4* vout) {
+        if (jr < 1 || jr > yn + 2) return;
+        const float* pm = ring0 + ((jr - 1) % kR2Slots0) * nx;
+        const float* pc = ring0 + (jr % kR2Slots0) * nx;
+        const float* pp = ring0 + ((jr + 1) % kR2Slots0) * nx;
+        float* l1 = ring1 + (jr % kR2Slots1) * nx;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            w0[j] = w1[j];
-            w1[j] = w2[j];
-            va[j] = vb[j];
-            vb[j] = vc[j];
+            if (!on[j]) continue;
+            const float4 c = lds4(pc + 4 * col[j]);
+            float left, right;
+            x_halo(pc, col[j], nq, nx, lane, c, left, right);
+            const float4 ym = lds4(pm + 4 * col[j]);
+            float4 pn;
+            float4 vv = vin[j];
+            update4(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, k0, rc, false);
+            *reinterpret_cast<float4*>(l1 + 4 * col[j]) = pn;
+            vout[j] = vv;
+        }
+    };
+    auto level2 = [&](int kr, const float4* vin) {
+        if (kr < 2 || kr > yn + 1) return;
+        const float* pm = ring1 + ((kr - 1) % kR2Slots1) * nx;
+        const float* pc = ring1 + (kr % kR2Slots1) * nx;
+        const float* pp = ring1 + ((kr + 1) % kR2Slots1) * nx;
+        const size_t ro = (size_t)(y0 - 2 + kr) * nx;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (!on[j]) continue;
+            const float4 c = lds4(pc + 4 * col[j]);
+            float left, right;
+            x_halo(pc, col[j], nq, nx, lane, c, left, right);
+            const float4 ym = lds4(pm + 4 * col[j]);
+            float4 pn;
+            float4 vv = vin[j];
+            update4(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, k1, rc, false);
+            stg4(phi_out + ro + 4 * col[j], pn);
+            stg4(v_out + ro + 4 * col[j], vv);
+        }
+    };
+
+    const int tmax = (yn + 5) / 2;  // last iteration: level-2 row 2t-3 or 2t-4 reaches yn+1
+    for (int t = 0; t <= tmax; ++t) {
+        bool ok = true;
+        for (int i = 2 * t; i <= 2 * t + 1; ++i)  // rows 2t, 2t+1 (rows below were waited earlier)
+            if (i < nload) ok = ok && mbar_wait(&bar[i % kR2Slots0], (i / kR2Slots0) & 1, err);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) drain_rows(bar, 2 * t, issued, err);
+            return;
+        }
+        // rows 2(t+kR2Ahead) and the next, into the slots of rows 2t-4 and 2t-3 (last read by
+        // level 1 at iteration t-1; level 1 now reads rows 2t-2 .. 2t+1)
+        if (tid == 0)
+            for (int i = 2 * (t + kR2Ahead); i <= 2 * (t + kR2Ahead) + 1 && i < nload; ++i) issue(i), issued = i;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) va0[j] = vb0[j], va1[j] = vb1[j];
+        load_v(2 * t + 1, vb0);  // for iteration t+1: rows 2t+1, 2t+2
+        load_v(2 * t + 2, vb1);
+        float4 no[ITEMS], ne[ITEMS];
+        level1(2 * t - 1, va0, no);
+        level1(2 * t, va1, ne);
+        level2(2 * t - 4, e0);
+        level2(2 * t - 3, o0);
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            e0[j] = e1[j];
+            e1[j] = ne[j];
+            o0[j] = no[j];
         }
     }
 }
+
+size_t smem2d_t2(int nx) { return 128 + (kR2Slots0 + kR2Slots1) * (size_t)nx * sizeof(float); }
 
 size_t smem_t2(int nx, int ty) { return 128 + 4 * (size_t)(ty + 4) * nx * 4 + 4 * (size_t)(ty + 2) * nx * 4; }
 
@@ -308,7 +327,6 @@ int pick_ty(const Geo& g)
 
 }  // namespace
 
-size_t smem2d_t2(int nx) { return 128 + (kT2Slots + 4) * (size_t)nx * sizeof(float); }
 
 bool tblock_ok(const Geo& g, int precision)
 {
@@ -325,10 +343,8 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
         static std::atomic<unsigned long long> attr1{0}, attr2{0};
         const size_t sm = smem2d_t2(g.nx);
         const int sms = sm_count_current();
-        // one CTA per SM (the two rings take 10 rows); chunks of rows for one full wave
         const int cy = (g.ny + sms - 1) / sms;
         const int blocks = (g.ny + cy - 1) / cy;
-        // the shared-memory limit is set once per device, to the largest row each variant takes
         if (g.nx / 4 > kTb2Threads) {
             const cudaError_t e =
                 smem_limit_once(attr2, (const void*)k_step2d_t2<2>, (int)smem2d_t2(8 * kTb2Threads));
