@@ -168,7 +168,7 @@ def declared_functions() -> list:
 def _check(rc: int, where: str, ok=(PRS_OK,)) -> int:
     if rc not in ok:
         detail = ""
-        if rc == PRS_ECUDA:
+        if rc in (PRS_ECUDA, PRS_ETIMEOUT):  # the library records the text of these
             detail = _lib.prs_last_error().decode()
         raise PRSError(rc, where, detail)
     return rc
