@@ -178,6 +178,14 @@ int prs_get_state(prs_sim* sim, void* h_phi, void* h_dphi, int64_t* n);
  * index (>= 0).  Bit-exact round trip with prs_get_state. */
 int prs_set_state(prs_sim* sim, const void* h_phi, const void* h_dphi, int64_t n);
 
+/* As prs_set_state, but queued on the run's stream without waiting: the call returns
+ * once the copies are issued.  The host arrays must stay valid and unchanged until the
+ * stream has passed the copies (any later call that synchronises the run, e.g.
+ * prs_step_measure, guarantees it).  From pinned host memory the copies overlap other
+ * runs' kernels, so one host thread can upload the next run's state while the current
+ * run steps; from pageable memory CUDA may complete them before returning. */
+int prs_set_state_async(prs_sim* sim, const void* h_phi, const void* h_dphi, int64_t n);
+
 /* Device pointers of the current fields and the step index (any output may be
  * NULL).  The pointers stay valid until the next prs_step or prs_destroy. */
 int prs_device_state(prs_sim* sim, void** d_phi, void** d_dphi, int64_t* n);

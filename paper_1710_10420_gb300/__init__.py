@@ -112,6 +112,7 @@ _SIGS = {
     "prs_step_measure": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(prs_diag)]),
     "prs_get_state": (ctypes.c_int, [_VP, _VP, _VP, _I64P]),
     "prs_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64]),
+    "prs_set_state_async": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64]),
     "prs_device_state": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I64P]),
     "prs_destroy": (ctypes.c_int, [_VP]),
     "prs_coefficients": (ctypes.c_int, [_P, ctypes.c_int64, _DP]),
@@ -237,6 +238,12 @@ def prs_get_state(sim, h_phi=None, h_dphi=None) -> int:
 
 def prs_set_state(sim, h_phi, h_dphi, n: int) -> None:
     _check(load().prs_set_state(sim, _ptr(h_phi), _ptr(h_dphi), n), "prs_set_state")
+
+
+def prs_set_state_async(sim, h_phi, h_dphi, n: int) -> None:
+    """Queue the upload and return; the arrays must stay alive and unchanged until the run
+    next synchronises (pinned memory, e.g. a torch tensor with pin_memory=True, overlaps)."""
+    _check(load().prs_set_state_async(sim, _ptr(h_phi), _ptr(h_dphi), n), "prs_set_state_async")
 
 
 def prs_device_state(sim):

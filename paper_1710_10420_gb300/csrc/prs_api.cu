@@ -273,7 +273,7 @@ static int prs_init_impl(prs_sim* s, const void* h_phi, const void* h_dphi)
     return PRS_OK;
 }
 
-static int prs_set_state_impl(prs_sim* s, const void* h_phi, const void* h_dphi, int64_t n)
+static int set_state_queued(prs_sim* s, const void* h_phi, const void* h_dphi, int64_t n, bool wait)
 {
     if (!s || !h_phi || !h_dphi || n < 0) return PRS_EINVAL;
     int rc = ensure_buffers(s);
@@ -281,10 +281,20 @@ static int prs_set_state_impl(prs_sim* s, const void* h_phi, const void* h_dphi,
     size_t bytes = (size_t)s->g.S * s->elem;
     PRS_CUDA(cudaMemcpyAsync(s->phi[s->cur], h_phi, bytes, cudaMemcpyHostToDevice, s->stream));
     PRS_CUDA(cudaMemcpyAsync(s->dphi, h_dphi, bytes, cudaMemcpyHostToDevice, s->stream));
-    PRS_CUDA(cudaStreamSynchronize(s->stream));
+    if (wait) PRS_CUDA(cudaStreamSynchronize(s->stream));
     s->n = n;
     s->initialised = true;
     return PRS_OK;
+}
+
+static int prs_set_state_impl(prs_sim* s, const void* h_phi, const void* h_dphi, int64_t n)
+{
+    return set_state_queued(s, h_phi, h_dphi, n, true);
+}
+
+extern "C" int prs_set_state_async(prs_sim* s, const void* h_phi, const void* h_dphi, int64_t n)
+{
+    return debug_after(s, set_state_queued(s, h_phi, h_dphi, n, false), "prs_set_state_async", true);
 }
 
 extern "C" int prs_get_state(prs_sim* s, void* h_phi, void* h_dphi, int64_t* n)

@@ -428,3 +428,27 @@ def test_two_host_threads_on_two_runs():
         sim.close()
         assert out[i] == alone[i][0]
         assert n == alone[i][1][2] and np.array_equal(phi, alone[i][1][0]) and np.array_equal(v, alone[i][1][1])
+
+
+def test_set_state_async():
+    """prs_set_state_async queues the upload and returns; a run set this way (from pinned
+    memory, two runs interleaved from one thread) steps exactly as one set with prs_set_state."""
+    import torch
+
+    shape = (256, 64, 24)
+    fshape = tuple(reversed(shape))
+    phi = torch.from_numpy(inp.random_field(shape, 17).astype(np.float32)).pin_memory()
+    v = torch.from_numpy((0.1 * inp.random_field(shape, 18)).astype(np.float32)).pin_memory()
+    ref = prs.Sim(shape, precision=prs.PRS_FP32)
+    ref.set_state(phi.numpy(), v.numpy(), 5)
+    dref = prs.prs_step_measure(ref.handle, 9).as_dict()
+    pref, vref, nref = ref.get_state()
+    ref.close()
+    runs = [prs.Sim(shape, precision=prs.PRS_FP32, stream=torch.cuda.Stream()) for _ in range(2)]
+    prs.prs_set_state_async(runs[0].handle, phi.numpy(), v.numpy(), 5)
+    prs.prs_set_state_async(runs[1].handle, phi.numpy(), v.numpy(), 5)
+    for r in runs:
+        assert prs.prs_step_measure(r.handle, 9).as_dict() == dref
+        p2, v2, n2 = r.get_state()
+        r.close()
+        assert n2 == nref and np.array_equal(p2, pref) and np.array_equal(v2, vref)
