@@ -60,8 +60,11 @@ extern "C" {
  * evaluate the wall diagnostics (Eqs. 7, 8) with correctly rounded division and
  * square root, as the generic diagnostic kernel does, instead of the fast kernels'
  * hardware reciprocal square root and approximate division.  The leapfrog step has
- * no division or square root, so the fields do not change.  Sec. III compares
- * single precision with and without correctly rounded divide and square root.
+ * no division or square root: with one step per pass (tblock = 1) the fields are
+ * bit-identical with and without the flag (prs_step_measure's diagnostics then run as
+ * a separate pass, which can change how later steps group into two-step passes).
+ * Sec. III compares single precision with and without correctly rounded divide and
+ * square root.
  * prs_step_measure then runs the diagnostics and the steps as separate passes.
  * Ensembles (prs_batch_create) reject it. */
 #define PRS_FP32_CR 2u
@@ -102,10 +105,11 @@ typedef struct {
     uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
     uint32_t flags;    /* PRS_REPRO | PRS_FP32_CR | PRS_DEBUG, or 0                 */
     int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (2 for
-                          FP32 2D boxes of at least 2^24 sites, else 1, see
-                          prs_default_tblock); 2 = two-step passes for FP32 boxes with an
-                          x side that is a multiple of 128 up to 1024 (3D) or 4096 (2D),
-                          else 1; at most 8 (values above 2 act as 2)               */
+                          FP32 3D boxes with x <= 512 and FP32 2D boxes of at least
+                          2^24 sites, else 1; see prs_default_tblock); 2 = two-step
+                          passes for FP32 boxes with an x side that is a multiple of
+                          128 up to 1024 (3D) or 4096 (2D), else 1; at most 8 (values
+                          above 2 act as 2)                                         */
 } prs_params;
 
 /* One output record of the wall diagnostics (Eq. 7, Eq. 8). */

@@ -15,18 +15,20 @@ int max_fused_steps(const Geo& g, int precision, bool repro)
     return tblock_ok(g, precision) ? 2 : 1;
 }
 
-// The library's default.  3D: one step per pass — the one-step kernel already moves
-// its 16 B per site-update at the measured copy bandwidth, while the two-step kernel (one
-// 512-thread CTA per SM, its rings filling shared memory) is limited by barrier and load
-// latency to about that same rate at 256^3 and 512^3 and runs slower at 1024^3.  2D: two
-// steps per pass once the state (three fields) outgrows L2 — rows are whole, so level 1
-// recomputes only the two rows outside each chunk (4096^2: 29 us against 48 us per step);
-// an L2-resident state (2048^2) steps faster one step at a time.
+// The library's default number of steps per pass.  FP32 3D: two for x sides up to 512
+// — measured 1.02-1.10x faster per step at 256^3 to 512x512x1024 and 1.56x at 128^3 (an
+// L2-resident state) — and one for 1024-wide rows, where the two rings leave room for
+// tiles of two rows only and the two-step pass is slower (0.81x at 1024x1024x256, and
+// 2.99 against 2.52 ms per step at 1024^3).  FP32 2D: two once the state (three fields)
+// outgrows L2 — rows are whole, so level 1 recomputes only the two rows outside each
+// chunk (4096^2: 28 us against 48 us per step); an L2-resident state (2048^2) steps
+// faster one step at a time.  FP64 and other boxes: one.
 int default_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)repro;
-    if (g.dims == 2 && precision == PRS_FP32 && tblock_ok(g, precision) && g.S >= (int64_t)1 << 24) return 2;
-    return 1;
+    if (precision != PRS_FP32 || !tblock_ok(g, precision)) return 1;
+    if (g.dims == 2) return g.S >= (int64_t)1 << 24 ? 2 : 1;
+    return g.nx <= 512 ? 2 : 1;
 }
 
 cudaError_t launch_step(const Geo& g, int precision, bool repro, const void* phi_in, void* phi_out, void* dphi,
