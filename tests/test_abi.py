@@ -83,3 +83,16 @@ def test_host_coefficients_follow_eq6():
     c = prs.prs_coefficients(prs.make_params((8, 8), era_m=2.0), 10)  # eta = 2
     assert c["delta"] == pytest.approx(0.5 * 3 * 0.1 * 2 / 2.0, rel=1e-15)
     assert prs.prs_coefficients(prs.make_params((8, 8), W0=math.inf), 0)["cV"] == 0.0
+
+
+def test_default_steps_per_pass(lib):
+    """The library's default steps per pass (host logic): two for FP32 3D boxes with x <= 512
+    and for FP32 2D boxes of at least 2^24 sites, one otherwise (1024-wide 3D rows, L2-sized 2D
+    states, FP64, boxes the staged kernels do not take)."""
+    cases = [((512, 512, 512), prs.PRS_FP32, 2), ((128, 128, 128), prs.PRS_FP32, 2),
+             ((256, 256, 1024), prs.PRS_FP32, 2), ((1024, 1024, 1024), prs.PRS_FP32, 1),
+             ((1024, 1024, 256), prs.PRS_FP32, 1), ((4096, 4096), prs.PRS_FP32, 2),
+             ((2048, 2048), prs.PRS_FP32, 1), ((512, 512, 512), prs.PRS_FP64, 1),
+             ((500, 500, 500), prs.PRS_FP32, 1), ((4096, 4096), prs.PRS_FP64, 1)]
+    for shape, precision, want in cases:
+        assert prs.prs_default_tblock(prs.make_params(shape, precision=precision)) == want, shape
