@@ -58,17 +58,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
 }
 
 // Wait for the phase with the given parity; false (and *err set) after kWaitLimitNs.
+// The clock is read once per 16 polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned int* err)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
+    for (;;) {
+#pragma unroll 1
+        for (int k = 0; k < 16; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
         if (global_ns() - t0 > kWaitLimitNs) {
             atomicOr(err, kErrWaitTimeout);
             return false;
         }
     }
-    return true;
 }
 
 // Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global

@@ -1,17 +1,27 @@
 // prs_tblock.cu -- two leapfrog steps (Eqs. 3-5) per pass over HBM, FP32 3D and 2D.
 //
 // One pass reads phi^n, dphi^{n-1/2} once and writes phi^{n+2}, dphi^{n+3/2} once:
-// 16 bytes per two site-updates.  A CTA owns ty whole x-rows of y and a chunk of
-// z-planes and marches along z through two levels:
-//   level 1 (step n)   on ty+2 rows, from level-0 planes staged by the TMA engine
-//                       (cp.async.bulk) in a 4-slot ring of ty+4 rows;
-//   level 2 (step n+1) on the ty output rows, from level-1 planes kept in a second
-//                       4-slot ring, two planes behind level 1, so each plane needs
-//                       one barrier.
-// dphi enters level 1 on ty+2 rows (its halo rows belong to neighbouring tiles), so
-// it is read from one buffer and written to another; the level-1 dphi stays in the
-// registers of the thread that owns its site until level 2 uses it.  The extra
-// level-1 rows (2 per ty) are recomputed by both tiles that need them.
+// 16 bytes per two site-updates.
+//
+// 3D: a CTA owns a tile of xw columns (the whole row, or a 128-multiple slice of it) by
+// ty rows and a chunk of z-planes, and marches along z through two levels:
+//   level 1 (step n)   on ty+2 rows, from level-0 phi planes of ty+4 rows in a 4-slot
+//                       ring and dphi^{n-1/2} planes of ty+2 rows in a 3-slot ring;
+//   level 2 (step n+1) on the ty output rows, one plane behind level 1, from level-1
+//                       planes kept in a 2-slot ring.
+// The TMA engine (cp.async.bulk) stages phi and dphi planes two iterations ahead, row
+// by row, the copies spread over the warps.  Every staged row holds the columns
+// [x0-4, x0+xw+4) (periodic in x), so a tile's edge columns find their x neighbours in
+// the same shared-memory row: a warp covers 32 float4 of one row and takes its x
+// neighbours by shuffle, lanes 0 and 31 from that row.  Shared memory serves only the x
+// and y neighbours: each thread keeps the values of its own columns at planes z-1, z,
+// z+1 in registers, for level 0 and for level 1, so one barrier per plane suffices.
+// Level 1 also computes the two columns just outside a sliced tile (x0-1 and x0+xw,
+// one lane per row and side), which level 2 needs as x neighbours; for whole rows those
+// are the row's own wrapped end columns.  dphi enters level 1 on ty+2 rows (its halo
+// rows belong to neighbouring tiles), so it is read from one buffer and written to
+// another; the level-1 dphi stays in the registers of the thread that owns its site
+// until level 2 uses it.
 #include <cuda_runtime.h>
 
 #include "prs_internal.h"
@@ -22,29 +32,39 @@ namespace prs {
 
 namespace {
 
-constexpr int kTbThreads = 512;
-constexpr int kTbItems = 3;  // float4 per thread per level-1 plane, at most
+constexpr int kTbThreads = 320;  // at most; a CTA has ceil((ty+2) * xw/4 / kTbItems) threads
+constexpr int kTbItems = 2;      // level-1 float4 per thread per plane
+constexpr int kTbMaxTy = 14;     // 2 (ty+2) halo columns per plane, one lane each of warp 0
+
+static __device__ __noinline__ void drain4(uint64_t* bar, int from, int issued, unsigned int* err)
+{
+    for (int i = from; i <= issued; ++i) mbar_wait(&bar[i & 3], (unsigned)(i >> 2) & 1u, err);
+}
 
 template <int ITEMS>
-__global__ void __launch_bounds__(kTbThreads, 1)
+__global__ void __launch_bounds__(kTbThreads, 2)
     k_step3d_t2(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
-                float* __restrict__ v_out, int nx, int ny, int nz, int ty, int cz, StepCoef<float> k0,
+                float* __restrict__ v_out, int nx, int ny, int nz, int xw, int ty, int cz, StepCoef<float> k0,
                 StepCoef<float> k1, RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    const int r1 = ty + 2, r0 = ty + 4;       // rows of a level-1 and a level-0 plane tile
-    const int t0 = r0 * nx, t1 = r1 * nx;      // floats per ring slot
-    float* ring0 = reinterpret_cast<float*>(smem_raw + 128);
-    float* ring1 = ring0 + 4 * t0;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int ytiles = ny / ty;
-    const int y0 = (blockIdx.x % ytiles) * ty;
-    const int z0 = (blockIdx.x / ytiles) * cz;
+    const int W = xw + 8;                  // floats per staged row: columns x0-4 .. x0+xw+3
+    const int r0 = ty + 4, r1 = ty + 2;    // rows of a level-0 and a level-1 plane tile
+    const int s0 = r0 * W, s1 = r1 * W;    // floats per ring slot
+    float* ring0 = reinterpret_cast<float*>(smem_raw + 128);  // phi^n: 4 slots
+    float* ring1 = ring0 + 4 * s0;                            // level 1: 2 slots
+    float* ringv = ring1 + 2 * s1;                            // dphi^{n-1/2}: 3 slots
+    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
+    const int nxt = nx / xw, ytiles = ny / ty;
+    const int x0 = (blockIdx.x % nxt) * xw;
+    const int y0 = (blockIdx.x / nxt % ytiles) * ty;
+    const int z0 = blockIdx.x / nxt / ytiles * cz;
     const int zn = min(cz, nz - z0);
-    const int nq = nx >> 2;
-    const int total = r1 * nq;  // level-1 float4 items of a plane
+    const int nq = xw >> 2;
+    const bool whole = xw == nx;
     const size_t plane = (size_t)nx * ny;
+    const int nplanes = zn + 4;  // level-0 local planes 0..zn+3 = global z0-2 .. z0+zn+1
 
     if (tid == 0) {
 #pragma unroll
@@ -55,101 +75,145 @@ __global__ void __launch_bounds__(kTbThreads, 1)
 
     auto wy = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
     auto wz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
-    const unsigned rowb = (unsigned)nx * 4u;
-    const int nload = zn + 4;  // level-0 local planes 0..zn+3 = global z0-2 .. z0+zn+1
-    auto issue = [&](int i) {
-        const float* src = phi_in + (size_t)wz(z0 - 2 + i) * plane;
-        float* dst = ring0 + (i & 3) * t0;
-        uint64_t* b = &bar[i & 3];
-        mbar_arrive_expect_tx(b, rowb * (unsigned)r0);
-        bulk_g2s(dst, src + (size_t)wy(y0 - 2) * nx, rowb, b);
-        bulk_g2s(dst + nx, src + (size_t)wy(y0 - 1) * nx, rowb, b);
-        bulk_g2s(dst + 2 * nx, src + (size_t)y0 * nx, rowb * (unsigned)ty, b);
-        bulk_g2s(dst + (size_t)(ty + 2) * nx, src + (size_t)wy(y0 + ty) * nx, rowb, b);
-        bulk_g2s(dst + (size_t)(ty + 3) * nx, src + (size_t)wy(y0 + ty + 1) * nx, rowb, b);
+    // Iteration i stages phi plane i+2 and, for the level-1 planes 1..zn+2, dphi plane
+    // i+1, both counted on bar[(i+2) % 4] (phi planes 0 and 1 go first, alone).  A staged
+    // row is [x0-4, x0+xw+4) modulo nx: at most three runs, each a multiple of 4 floats
+    // at a 16-byte boundary, at the same columns in every row.  Thread c < 3 (r0 + r1)
+    // owns run c % 3 of staged row c / 3 (phi rows first, then dphi rows) for the whole
+    // pass, so staging a plane costs each copying thread one instruction sequence; thread
+    // 0 arms the barrier with the bytes (copies landing before it leave the count
+    // negative, which holds the phase open).
+    int cp_len = 0, cp_src = 0, cp_dst = 0;  // floats; source offset within a plane
+    bool cp_v = false;
+    {
+        const int r = tid / 3, u = tid - 3 * (tid / 3);
+        int x = x0 >= 4 ? x0 - 4 : x0 - 4 + nx, p = 0;
+        for (int run = 0; run < u && p < W; ++run) {
+            p += min(W - p, nx - x);
+            x = 0;
+        }
+        if (r < r0 + r1 && p < W) {
+            cp_len = min(W - p, nx - x);
+            cp_v = r >= r0;
+            cp_src = (cp_v ? wy(y0 - 1 + r - r0) : wy(y0 - 2 + r)) * nx + x;
+            cp_dst = (cp_v ? r - r0 : r) * W + p;
+        }
+    }
+    auto issue = [&](int pl, bool with_v) {
+        uint64_t* b = &bar[pl & 3];
+        if (tid == 0) mbar_arrive_expect_tx(b, (unsigned)(s0 + (with_v ? s1 : 0)) * 4u);
+        if (cp_len == 0 || (cp_v && !with_v)) return;
+        const float* src = cp_v ? v_in + (size_t)wz(z0 - 3 + pl) * plane : phi_in + (size_t)wz(z0 - 2 + pl) * plane;
+        float* dst = cp_v ? ringv + ((pl - 1) % 3) * s1 : ring0 + (pl & 3) * s0;
+        bulk_g2s(dst + cp_dst, src + cp_src, (unsigned)cp_len * 4u, b);
     };
-    int issued = -1;
-    if (tid == 0) issue(0), issued = 0;
-
-    int row[ITEMS], col[ITEMS];
-    bool on[ITEMS];
+    issue(0, false);
+    issue(1, false);
+    int issued = 1;
+    // This thread's level-1 sites: float4 column col of level-1 row row (level-0 row
+    // row+1, global row y0-1+row); whole warps share a row.
+    int off[ITEMS], go[ITEMS];
+    bool on[ITEMS], out[ITEMS], first[ITEMS], last[ITEMS];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        const int q = tid + kTbThreads * j;
-        on[j] = q < total;  // whole warps: nq and the block size are multiples of 32
-        row[j] = on[j] ? q / nq : 0;
-        col[j] = on[j] ? q - row[j] * nq : 0;
+        const int q = tid + nthr * j;
+        on[j] = q < r1 * nq;
+        const int row = on[j] ? q / nq : 0, col = on[j] ? q - row * nq : 0;
+        out[j] = on[j] && row >= 1 && row <= ty;
+        first[j] = col == 0;
+        last[j] = col == nq - 1;
+        off[j] = row * W + 4 + 4 * col;  // in a level-1 or dphi slot; +W in a level-0 slot
+        go[j] = (y0 - 1 + row) * nx + x0 + 4 * col;  // in a plane, for the output rows
     }
-    // dphi^{n-1/2} of the level-1 sites: the plane used now and the one loaded ahead
-    float4 va[ITEMS], vb[ITEMS];
-    // level-1 dphi^{n+1/2} of this thread's sites for the last three level-1 planes
-    float4 w0[ITEMS], w1[ITEMS], w2[ITEMS];
-    auto load_v = [&](int jl, float4* dst) {  // level-0 local plane jl, level-1 rows
-        const float* vp = v_in + (size_t)wz(z0 - 2 + jl) * plane;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j)
-            if (on[j]) dst[j] = ldg_stream4(vp + (size_t)wy(y0 - 1 + row[j]) * nx + 4 * col[j]);
-    };
+    // Halo columns of a sliced tile: lane h < 2 r1 of warp 0 owns level-1 row h/2 at
+    // column x0-1 (h even) or x0+xw (h odd).
+    const bool hal = !whole && tid < 2 * r1;
+    const int hoff = (lane >> 1) * W + ((lane & 1) ? xw + 4 : 3);  // in a level-1 or dphi slot
 
-    for (int i = 0; i <= zn + 4; ++i) {
-        bool ok = true;
-        if (i < nload) ok = mbar_wait(&bar[i & 3], (i >> 2) & 1, err);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 f0m[ITEMS], f0c[ITEMS];  // level 0 at planes j-1, j of the level-1 plane j
+    float4 f1m[ITEMS], f1c[ITEMS];  // level 1 at planes k-1, k of the level-2 plane k
+    float4 w1[ITEMS];               // level-1 dphi^{n+1/2} at plane k
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) f0m[j] = f0c[j] = f1m[j] = f1c[j] = w1[j] = z4;
+    float h0m = 0.f, h0c = 0.f;  // level 0 at planes j-1, j of a halo lane's column
+
+    for (int i = 0; i < nplanes; ++i) {
+        const bool ok = mbar_wait(&bar[i & 3], (unsigned)(i >> 2) & 1u, err);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) drain(bar, i, issued, err);
+            if (tid == 0) drain4(bar, i, issued, err);
             return;
         }
-        if (tid == 0 && i + 1 < nload) issue(i + 1), issued = i + 1;
-        const int j1 = i - 1;  // level-1 plane of this iteration
-        const int k2 = i - 3;  // level-2 plane of this iteration
-        const bool next_v = i >= 1 && i <= zn + 2;  // dphi of the next level-1 plane, one iteration ahead
-        if (next_v) load_v(i, vb);
-        if (j1 >= 1 && j1 <= zn + 2) {
-            const float* pm = ring0 + ((j1 - 1) & 3) * t0;
-            const float* pc = ring0 + (j1 & 3) * t0;
-            const float* pp = ring0 + ((j1 + 1) & 3) * t0;
-            float* l1 = ring1 + (j1 & 3) * t1;
+        if (i + 2 < nplanes) issue(i + 2, i + 1 >= 1 && i + 1 <= zn + 2), issued = i + 2;
+        const int j = i - 1;  // level-1 plane of this iteration
+        const int k = i - 2;  // level-2 plane of this iteration
+        const float* Pn = ring0 + (i & 3) * s0 + W;        // level-0 plane j+1, from row 1
+        const float* Pj = ring0 + ((i + 3) & 3) * s0 + W;  // level-0 plane j, from row 1
+        float4 f0p[ITEMS], f1p[ITEMS], w1n[ITEMS];
 #pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                if (!on[j]) continue;
-                const int off = (row[j] + 1) * nx + 4 * col[j];  // level-0 row of this level-1 site
-                const float4 c = lds4(pc + off);
-                float left, right;
-                x_halo(pc + (row[j] + 1) * nx, col[j], nq, nx, lane, c, left, right);
+        for (int q = 0; q < ITEMS; ++q) {
+            f0p[q] = on[q] ? lds4(Pn + off[q]) : z4;
+            f1p[q] = w1n[q] = z4;
+        }
+        const float h0p = hal ? Pn[hoff] : 0.f;
+        if (j >= 1 && j <= zn + 2) {
+            float* L1 = ring1 + (j & 1) * s1;
+            const float* V = ringv + (j % 3) * s1;
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                if (!on[q]) continue;  // warp-uniform
+                const float* c0 = Pj + off[q];
+                const float4 c = f0c[q];
+                float left = __shfl_up_sync(0xffffffffu, c.w, 1);
+                float right = __shfl_down_sync(0xffffffffu, c.x, 1);
+                if (lane == 0) left = c0[-1];
+                if (lane == 31) right = c0[4];
                 float4 pn;
-                float4 vv = va[j];
-                update4(c, left, right, lds4(pc + off + nx), lds4(pc + off - nx), lds4(pp + off), lds4(pm + off), vv,
-                        pn, k0, rc, true);
-                *reinterpret_cast<float4*>(l1 + row[j] * nx + 4 * col[j]) = pn;
-                w2[j] = vv;
+                float4 vv = lds4(V + off[q]);
+                update4(c, left, right, lds4(c0 + W), lds4(c0 - W), f0p[q], f0m[q], vv, pn, k0, rc, true);
+                *reinterpret_cast<float4*>(L1 + off[q]) = pn;
+                if (whole) {  // the wrapped end columns of the row, for level 2's x neighbours
+                    if (first[q]) L1[off[q] + xw] = pn.x;
+                    if (last[q]) L1[off[q] - xw + 3] = pn.w;
+                }
+                f1p[q] = pn;
+                w1n[q] = vv;
+            }
+            if (hal) {
+                const float* c0 = Pj + hoff;
+                float vv = V[hoff];
+                L1[hoff] = update1(h0c, c0[1], c0[-1], c0[W], c0[-W], h0p, h0m, vv, k0, rc, true);
             }
         }
-        if (k2 >= 2 && k2 <= zn + 1) {
-            const float* pm = ring1 + ((k2 - 1) & 3) * t1;
-            const float* pc = ring1 + (k2 & 3) * t1;
-            const float* pp = ring1 + ((k2 + 1) & 3) * t1;
-            const size_t zo = (size_t)(z0 - 2 + k2) * plane;
+        if (k >= 2 && k <= zn + 1) {
+            const float* L1 = ring1 + (k & 1) * s1;
+            const size_t zo = (size_t)(z0 - 2 + k) * plane;
 #pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                if (!on[j] || row[j] < 1 || row[j] > ty) continue;  // warp-uniform: one row per warp
-                const int off = row[j] * nx + 4 * col[j];
-                const float4 c = lds4(pc + off);
-                float left, right;
-                x_halo(pc + row[j] * nx, col[j], nq, nx, lane, c, left, right);
+            for (int q = 0; q < ITEMS; ++q) {
+                if (!out[q]) continue;  // warp-uniform
+                const float* c1p = L1 + off[q];
+                const float4 c = f1c[q];
+                float left = __shfl_up_sync(0xffffffffu, c.w, 1);
+                float right = __shfl_down_sync(0xffffffffu, c.x, 1);
+                if (lane == 0) left = c1p[-1];
+                if (lane == 31) right = c1p[4];
                 float4 pn;
-                float4 vv = w0[j];
-                update4(c, left, right, lds4(pc + off + nx), lds4(pc + off - nx), lds4(pp + off), lds4(pm + off), vv,
-                        pn, k1, rc, true);
-                const size_t go = zo + (size_t)(y0 + row[j] - 1) * nx + 4 * col[j];
-                stg4(phi_out + go, pn);
-                stg4(v_out + go, vv);
+                float4 vv = w1[q];
+                update4(c, left, right, lds4(c1p + W), lds4(c1p - W), f1p[q], f1m[q], vv, pn, k1, rc, true);
+                stg4(phi_out + zo + go[q], pn);
+                stg4(v_out + zo + go[q], vv);
             }
         }
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            w0[j] = w1[j];
-            w1[j] = w2[j];
-            if (next_v) va[j] = vb[j];
+        for (int q = 0; q < ITEMS; ++q) {
+            f0m[q] = f0c[q];
+            f0c[q] = f0p[q];
+            f1m[q] = f1c[q];
+            f1c[q] = f1p[q];
+            w1[q] = w1n[q];
         }
+        h0m = h0c;
+        h0c = h0p;
     }
 }
 
@@ -308,21 +372,35 @@ __global__ void __launch_bounds__(kTb2Threads, 1)
 
 size_t smem2d_t2(int nx) { return 128 + (kR2Slots0 + kR2Slots1) * (size_t)nx * sizeof(float); }
 
-size_t smem_t2(int nx, int ty) { return 128 + 4 * (size_t)(ty + 4) * nx * 4 + 4 * (size_t)(ty + 2) * nx * 4; }
+constexpr size_t kTbSmemMax = 160 * 1024;
 
-constexpr size_t kTbSmemMax = 200 * 1024;
+// Tile of a 3D two-step pass: xw columns (the whole row up to 256, else the widest
+// 128-multiple up to 256 that divides nx: two CTAs per SM hide each other's barrier
+// waits) by ty rows (the largest divisor of ny whose level-1 plane takes at most
+// kTbItems float4 per thread of a kTbThreads CTA; a sliced tile has one halo lane of
+// warp 0 per level-1 row and side).
+struct Tile3 {
+    int xw, ty, threads;
+    size_t smem;
+};
 
-// Rows per tile: the largest power of two dividing ny whose rings fit and whose
-// level-1 plane has at most kTbItems float4 per thread.
-int pick_ty(const Geo& g)
+bool plan3(const Geo& g, Tile3* t)
 {
-    for (int ty = 32; ty >= 1; ty >>= 1) {
-        if (g.ny % ty != 0 || ty > g.ny) continue;
-        if (smem_t2(g.nx, ty) > kTbSmemMax) continue;
-        if ((ty + 2) * (g.nx / 4) > kTbItems * kTbThreads) continue;
-        return ty;
-    }
-    return 0;
+    if (g.nx % 128 != 0 || g.nz < 3) return false;
+    int xw = 0;
+    for (int w = 256; w >= 128 && !xw; w -= 128)
+        if (g.nx % w == 0) xw = w;
+    const int nq = xw / 4;
+    const int tymax = xw == g.nx ? 28 : kTbMaxTy;
+    int ty = 0;
+    for (int c = tymax < g.ny ? tymax : g.ny; c >= 1 && !ty; --c)
+        if (g.ny % c == 0 && (c + 2) * nq <= kTbItems * kTbThreads) ty = c;
+    if (!ty) return false;
+    t->xw = xw;
+    t->ty = ty;
+    t->threads = (((ty + 2) * nq + kTbItems - 1) / kTbItems + 31) / 32 * 32;
+    t->smem = 128 + (size_t)(4 * (ty + 4) + 5 * (ty + 2)) * (xw + 8) * sizeof(float);
+    return t->smem <= kTbSmemMax;
 }
 
 }  // namespace
@@ -332,7 +410,8 @@ bool tblock_ok(const Geo& g, int precision)
 {
     if (precision != PRS_FP32 || g.nx % 128 != 0) return false;
     if (g.dims == 2) return g.nx <= 2 * kTb2Threads * 4;  // at most two float4 per thread of a row
-    return g.nx <= 1024 && g.nz >= 3 && pick_ty(g) > 0;
+    Tile3 t;
+    return plan3(g, &t);
 }
 
 cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
@@ -365,25 +444,32 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
         const cudaError_t e = smem_limit_once(attr, (const void*)k_step3d_t2<kTbItems>, (int)kTbSmemMax);
         if (e != cudaSuccess) return e;
     }
-    const int ty = pick_ty(g);
-    if (ty == 0) return cudaErrorInvalidValue;
-    const int sms = sm_count_current();
-    const int ytiles = g.ny / ty;
-    // z-chunks: whole waves of one CTA per SM, balanced against the four halo planes
+    Tile3 t;
+    if (!plan3(g, &t)) return cudaErrorInvalidValue;
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_step3d_t2<kTbItems>, t.threads,
+                                                      t.smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int slots = per_sm * sm_count_current();
+    const int tiles = (g.nx / t.xw) * (g.ny / t.ty);
+    // z-chunks: whole waves of resident CTAs, balanced against the four halo planes per chunk
     int best = 1;
     double best_score = -1.0;
     for (int nc = 1; nc <= g.nz / 8 || nc == 1; ++nc) {
         const int c = (g.nz + nc - 1) / nc, n = (g.nz + c - 1) / c;
-        const long long blocks = (long long)ytiles * n;
-        const long long waves = (blocks + sms - 1) / sms;
-        const double score = (double)blocks / (double)(waves * sms) * c / (c + 4.0) * (waves >= 2 ? 1.0 : 0.9);
+        const long long blocks = (long long)tiles * n;
+        const long long waves = (blocks + slots - 1) / slots;
+        const double score = (double)blocks / (double)(waves * slots) * c / (c + 4.0) * (waves >= 2 ? 1.0 : 0.9);
         if (score > best_score + 1e-9) best_score = score, best = n;
         if (nc > 4096) break;
     }
     const int cz = (g.nz + best - 1) / best;
-    const int blocks = ytiles * ((g.nz + cz - 1) / cz);
-    k_step3d_t2<kTbItems><<<blocks, kTbThreads, smem_t2(g.nx, ty), st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny,
-                                                                         g.nz, ty, cz, k0, k1, rc, err);
+    const long long blocks = (long long)tiles * ((g.nz + cz - 1) / cz);
+    if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
+    k_step3d_t2<kTbItems><<<(unsigned)blocks, t.threads, t.smem, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, g.nz,
+                                                                       t.xw, t.ty, cz, k0, k1, rc, err);
     return cudaGetLastError();
 }
 

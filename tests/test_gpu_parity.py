@@ -131,7 +131,8 @@ def test_fp32_close(shape, era_m):
 @pytest.mark.parametrize("nsteps", [23, 8, 6, 3, 2, 1])
 @pytest.mark.parametrize("tblock", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(256, 256), (64, 48, 40), (128, 64, 40), (256, 32, 24), (512, 16, 12),
-                                   (1024, 8, 10), (128, 32, 3), (256, 48, 7),
+                                   (1024, 8, 10), (128, 32, 3), (256, 48, 7), (384, 12, 7), (256, 7, 4),
+                                   (640, 8, 6), (768, 10, 5), (2048, 6, 3),
                                    (512, 96), (4096, 12), (1024, 5), (2048, 40), (128, 3)])
 def test_fp32_temporal_blocks(shape, tblock, nsteps):
     """Every fused-steps-per-pass setting (and the mix of one- and two-step passes it implies)
@@ -143,9 +144,10 @@ def test_fp32_temporal_blocks(shape, tblock, nsteps):
     assert _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
 
 
-def test_two_step_passes_match_single_steps():
-    """Two-step passes and one-step passes agree to FP32 rounding over many passes (3D, bound buffers)."""
-    shape = (256, 64, 48)
+@pytest.mark.parametrize("shape", [(256, 64, 48), (1024, 32, 24)])
+def test_two_step_passes_match_single_steps(shape):
+    """Two-step passes and one-step passes agree to FP32 rounding over many passes (3D: whole rows
+    and rows in 512-column tiles)."""
     a = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=1)
     b = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=2)
     assert _rel(b[0], a[0].astype(np.float64)) <= 1e-5 and _rel(b[1], a[1].astype(np.float64)) <= 1e-5
