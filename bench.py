@@ -233,11 +233,13 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-# the sources that define the one-step FP32 kernel (device code and the structs it takes)
-STEP_KERNEL_SOURCES = ("prs_fast.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_reduce.cuh")
+# the sources that define the FP32 step kernels (device code and the structs they take),
+# by steps per pass
+STEP_KERNEL_SOURCES = {1: ("prs_fast.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_reduce.cuh"),
+                       2: ("prs_tblock.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h")}
 
 
-def kernel_sources_sha(names=STEP_KERNEL_SOURCES) -> str:
+def kernel_sources_sha(names=STEP_KERNEL_SOURCES[2]) -> str:
     csrc = os.path.join(ROOT, "paper_1710_10420_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(names):
@@ -246,16 +248,18 @@ def kernel_sources_sha(names=STEP_KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_record(workload: str):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if the kernel's
-    sources are unchanged since the counters were taken."""
+def traffic_record(workload: str, tblock: int):
+    """Per-launch DRAM bytes of the step kernel (tblock steps per pass) from the committed ncu
+    summary, if the kernel's sources are unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get(workload)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("sources_sha") != kernel_sources_sha(tuple(rec.get("sources", STEP_KERNEL_SOURCES))):
+    if not rec or rec.get("tblock", 1) != tblock:
+        return None
+    if rec.get("sources_sha") != kernel_sources_sha(tuple(rec.get("sources", STEP_KERNEL_SOURCES[tblock]))):
         return None
     return rec
 
@@ -276,26 +280,35 @@ def run_gpu(args, world, rank, local):
     tb = args.tblock if args.tblock > 0 else lib_default_tblock(prs, shape)
     # one bench step = the diagnostics of the state at the start of an output interval,
     # fused into its first leapfrog step (prs_step_measure), then the other interval-1
-    # steps (prs_step); events bracket the two calls separately
+    # steps (prs_step)
     rest = args.interval - 1
     pairs = rest // 2 if tb == 2 else 0  # the library's split of prs_step(rest) into passes
     if pairs % 2 and rest == 2 * pairs:
         pairs -= 1
     singles = rest - 2 * pairs
     step_launches = pairs + singles
+    # the rest runs as two calls with the same passes as prs_step(rest): first `pure` steps
+    # that are all passes of the step kernel (with two steps per pass an even number of
+    # pairs, which the library splits no further), then the remaining `tail`; events
+    # bracket the three calls, so the middle bracket times the step kernel alone
+    pure = 2 * (pairs - pairs % 2) if tb == 2 else rest
+    tail = rest - pure
+    pure_launches = pure // tb
 
     def one_step(events=None):
-        if events is None:
-            d = prs.prs_step_measure(sim.handle, 1)
-            prs.prs_step(sim.handle, rest)
-            return d
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record(stream)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if events is not None else [None] * 4
+        rec = (lambda ev: ev.record(stream)) if events is not None else (lambda ev: None)
+        rec(e[0])
         d = prs.prs_step_measure(sim.handle, 1)
-        e[1].record(stream)
-        prs.prs_step(sim.handle, rest)
-        e[2].record(stream)
-        events.append(e)
+        rec(e[1])
+        if pure:
+            prs.prs_step(sim.handle, pure)
+        rec(e[2])
+        if tail:
+            prs.prs_step(sim.handle, tail)
+        rec(e[3])
+        if events is not None:
+            events.append(e)
         return d
 
     for _ in range(args.warmup):
@@ -314,26 +327,37 @@ def run_gpu(args, world, rank, local):
     barrier(world)
     ms = start.elapsed_time(stop)
     ms_max = allreduce_max(ms, world, dev)
-    # every launch inside the bracketed prs_step calls is the step kernel (for interval = 20:
-    # nineteen one-step passes), so its mean duration is the total / launches
-    step_ms = sum(e[1].elapsed_time(e[2]) for e in events)
-    launch_avg_ms = step_ms / (len(events) * step_launches)
+    # the middle bracket holds only launches of the step kernel (for interval = 20 and two
+    # steps per pass: eight two-step passes), so its mean launch duration is total / launches
     fused_ms = sum(e[0].elapsed_time(e[1]) for e in events) / len(events)
-    units_per_launch = rest / step_launches  # leapfrog steps per plain pass, on average over the interval
+    tail_ms = sum(e[2].elapsed_time(e[3]) for e in events) / len(events)
+    if pure_launches:
+        launch_avg_ms = sum(e[1].elapsed_time(e[2]) for e in events) / (len(events) * pure_launches)
+    else:  # an interval too short for a pure bracket: the plain passes' mean
+        launch_avg_ms = tail_ms / max(step_launches, 1)
     value = aggregate(sites * args.interval * args.steps, world, ms_max / 1e3)
 
     peak, peak_kind = peaks()
-    achieved = BYTES_PER_SITE_UPDATE[0] * sites * units_per_launch / (launch_avg_ms / 1e3) / 1e9
-    rec = traffic_record(args.workload)
+    # algorithmic bytes of one pass: phi^n and dphi read once, phi and dphi written once,
+    # whatever the steps per pass (16 B per site-update at one step, 8 B at two)
+    alg_bytes = BYTES_PER_SITE_UPDATE[0] * sites
+    achieved = alg_bytes / (launch_avg_ms / 1e3) / 1e9
+    effective = alg_bytes * tb / (launch_avg_ms / 1e3) / 1e9
+    rec = traffic_record(args.workload, tb)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (rec["dram_bytes_per_launch"] if rec else None),
-                "kernel": f"fused PRS step, {units_per_launch:g} leapfrog step(s) per pass on average",
-                "algorithmic_bytes_per_launch": BYTES_PER_SITE_UPDATE[0] * sites * units_per_launch,
-                "note": "achieved = 16 B x site-updates of one launch / its mean duration; with two steps per "
-                        "pass this effective figure can exceed the copy bandwidth, dram_frac is the measured one",
+                "kernel": ("k_step3d_t2, two leapfrog steps per pass" if tb == 2 else
+                           "k_step3d_f32, one leapfrog step per pass") if len(shape) == 3 else
+                          f"2D step kernel, {tb} leapfrog step(s) per pass",
+                "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_site_update": alg_bytes / (sites * tb),
+                "launches_timed": len(events) * (pure_launches or step_launches),
+                "note": "achieved = the pass's algorithmic bytes (16 B per site, read and write of phi and dphi) "
+                        "/ its mean launch duration; effective = 16 B x site-updates / duration, the copy "
+                        "bandwidth a one-step pass would need for the same rate",
+                "effective_gbs": effective, "effective_frac": effective / peak,
                 "launch_ms": launch_avg_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)",
                 "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                "fused_step_and_diagnostics_ms": fused_ms}
+                "fused_step_and_diagnostics_ms": fused_ms, "tail_passes_ms": tail_ms}
     if rec:
         roofline["dram_frac"] = rec["dram_bytes_per_launch"] / (launch_avg_ms / 1e3) / 1e9 / peak
 

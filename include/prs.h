@@ -105,10 +105,11 @@ typedef struct {
     uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
     uint32_t flags;    /* PRS_REPRO | PRS_FP32_CR | PRS_DEBUG, or 0                 */
     int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (2 for
-                          FP32 3D boxes with x <= 512 and FP32 2D boxes of at least
-                          2^24 sites, else 1; see prs_default_tblock); 2 = two-step
-                          passes for FP32 boxes with an x side that is a multiple of
-                          128 up to 1024 (3D) or 4096 (2D), else 1; at most 8 (values
+                          FP32 3D boxes whose two-step tiles get at least 4 rows of y
+                          and FP32 2D boxes of at least 2^24 sites, else 1; see
+                          prs_default_tblock); 2 = two-step passes for FP32 boxes with
+                          an x side that is a multiple of 128 (3D; z side >= 3) or a
+                          multiple of 128 up to 4096 (2D), else 1; at most 8 (values
                           above 2 act as 2)                                         */
 } prs_params;
 

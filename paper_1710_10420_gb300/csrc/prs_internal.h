@@ -102,8 +102,10 @@ cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, 
                                      StepCoef<float> k, RunConst<float> rc, const DiagScratch& scr, unsigned int* err,
                                      cudaStream_t st);
 
-// Two fused leapfrog steps per pass (prs_tblock.cu), FP32 3D; dphi out of place.
+// Two fused leapfrog steps per pass (prs_tblock.cu), FP32 3D and 2D; dphi out of place.
 bool tblock_ok(const Geo& g, int precision);
+// Rows of y per tile of the 3D two-step pass (0 when it does not apply).
+int tblock3_rows(const Geo& g);
 cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
                            StepCoef<float> k0, StepCoef<float> k1, RunConst<float> rc, unsigned int* err,
                            cudaStream_t st);

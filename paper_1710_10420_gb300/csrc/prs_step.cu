@@ -15,20 +15,20 @@ int max_fused_steps(const Geo& g, int precision, bool repro)
     return tblock_ok(g, precision) ? 2 : 1;
 }
 
-// The library's default number of steps per pass.  FP32 3D: two for x sides up to 512
-// — measured 1.02-1.10x faster per step at 256^3 to 512x512x1024 and 1.56x at 128^3 (an
-// L2-resident state) — and one for 1024-wide rows, where the two rings leave room for
-// tiles of two rows only and the two-step pass is slower (0.81x at 1024x1024x256, and
-// 2.99 against 2.52 ms per step at 1024^3).  FP32 2D: two once the state (three fields)
-// outgrows L2 — rows are whole, so level 1 recomputes only the two rows outside each
-// chunk (4096^2: 28 us against 48 us per step); an L2-resident state (2048^2) steps
-// faster one step at a time.  FP64 and other boxes: one.
+// The library's default number of steps per pass.  FP32 3D: two wherever the two-step
+// pass gets tiles of at least 4 rows (fewer rows make level 1 recompute more than it
+// saves) — per step against one step per pass, measured 14.5 against 22.1 us at 128^3,
+// 46.3 against 49.1 us at 256^3, 0.269 against 0.323 ms at 512^3 and 1.96 against 2.53 ms
+// at 1024^3.  FP32 2D: two once the state (three fields) outgrows L2 — rows are
+// whole, so level 1 recomputes only the two rows outside each chunk (4096^2: 28 us
+// against 48 us per step); an L2-resident state (2048^2) steps faster one step at a
+// time.  FP64 and other boxes: one.
 int default_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)repro;
     if (precision != PRS_FP32 || !tblock_ok(g, precision)) return 1;
     if (g.dims == 2) return g.S >= (int64_t)1 << 24 ? 2 : 1;
-    return g.nx <= 512 ? 2 : 1;
+    return tblock3_rows(g) >= 4 ? 2 : 1;
 }
 
 cudaError_t launch_step(const Geo& g, int precision, bool repro, const void* phi_in, void* phi_out, void* dphi,

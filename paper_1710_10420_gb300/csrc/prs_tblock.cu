@@ -414,6 +414,12 @@ bool tblock_ok(const Geo& g, int precision)
     return plan3(g, &t);
 }
 
+int tblock3_rows(const Geo& g)
+{
+    Tile3 t;
+    return g.dims == 3 && plan3(g, &t) ? t.ty : 0;
+}
+
 cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
                            StepCoef<float> k0, StepCoef<float> k1, RunConst<float> rc, unsigned int* err,
                            cudaStream_t st)

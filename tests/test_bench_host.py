@@ -66,8 +66,11 @@ def test_kernel_source_hash_and_traffic_record(bench):
         rec = json.load(f)["3d1024"]
     for name in rec["sources"]:
         assert os.path.exists(os.path.join(ROOT, "paper_1710_10420_gb300", "csrc", name))
-    # a record is used only while its kernel's sources are unchanged
-    assert (bench.traffic_record("3d1024") is not None) == (rec["sources_sha"] == bench.kernel_sources_sha())
+    # a record is used only for its steps per pass and while its kernel's sources are unchanged
+    tb = rec.get("tblock", 1)
+    same = rec["sources_sha"] == bench.kernel_sources_sha(tuple(rec["sources"]))
+    assert (bench.traffic_record("3d1024", tb) is not None) == same
+    assert bench.traffic_record("3d1024", 3 - tb) is None
 
 
 def test_reference_arm_prints_one_json_line():
