@@ -389,8 +389,7 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
         step_coefficients(s->p, n + 1, b);
         cudaError_t e = launch_step_t2(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
                                        (const float*)vbuf[k & 1], (float*)vbuf[1 - (k & 1)],
-                                       StepCoef<float>{(float)a[0], (float)a[1], (float)a[2]},
-                                       StepCoef<float>{(float)b[0], (float)b[1], (float)b[2]}, rcf, err, s->stream);
+                                       kick_f32(a, s->rc), kick_f32(b, s->rc), rcf, err, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
         s->cur = 1 - s->cur;
     }
@@ -492,7 +491,7 @@ static int prs_step_measure_impl(prs_sim* s, int64_t nsteps, prs_diag* out)
                            (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
         e = launch_step_measure_fast(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
                                      (const float*)s->dphi, (float*)s->dphi,
-                                     StepCoef<float>{(float)c[0], (float)c[1], (float)c[2]}, rc, s->scr,
+                                     kick_f32(c, s->rc), rc, s->scr,
                                      &s->d_status->error, s->stream);
     }
     if (e == cudaErrorNotSupported) {

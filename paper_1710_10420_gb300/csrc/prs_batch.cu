@@ -57,7 +57,7 @@ struct BRun {
     long long nitems;  // items per tile: steps + 1 (the last only measures)
     float* phi[2];     // phi[n & 1] holds phi^n (n counted from the start of the call)
     float* v;
-    const float* coef;  // c1, c2, cV of local step n at coef[3n..3n+2]
+    const float* coef;  // the FP32 kick (KickF) of local step n at coef[4n..4n+3]
     RunConst<float> rc;
     unsigned int* progress;  // per tile: items completed
     DiagAcc* partial;        // [output][tile]
@@ -153,8 +153,8 @@ template <bool STEP, bool MEAS>
 __device__ bool run_tile(const BRun& R, int i, long long n, unsigned char* smem, unsigned* wq, SiteAcc& a,
                          unsigned int* err)
 {
-    StepCoef<float> k{};
-    if (STEP) k = StepCoef<float>{R.coef[3 * n], R.coef[3 * n + 1], R.coef[3 * n + 2]};
+    KickF k{};
+    if (STEP) k = KickF{R.coef[4 * n], R.coef[4 * n + 1], R.coef[4 * n + 2], R.coef[4 * n + 3]};
     const float* pin = R.phi[n & 1];
     float* pout = R.phi[(n + 1) & 1];
     if (R.dims == 3) {
@@ -340,9 +340,11 @@ static void plan(const prs_batch* b, const int64_t* nsteps, int64_t measure_ever
         for (int64_t k = 0; k < nsteps[r]; ++k) {
             double c[5];
             step_coefficients(b->p[r], b->n[r] + k, c);
-            S.coef.push_back((float)c[0]);
-            S.coef.push_back((float)c[1]);
-            S.coef.push_back((float)c[2]);
+            const KickF kf = kick_f32(c, rcd);
+            S.coef.push_back(kf.c1);
+            S.coef.push_back(kf.g);
+            S.coef.push_back(kf.k1);
+            S.coef.push_back(kf.k2);
         }
         S.prog_off[r] = off;
         off += align256(sizeof(unsigned) * (size_t)u.ntiles);

@@ -18,7 +18,7 @@ namespace prs {
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
     k_step3d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out, int nx,
-                 int ny, int nz, int ty, int cz, StepCoef<float> k, RunConst<float> rc, unsigned int* err)
+                 int ny, int nz, int ty, int cz, KickF k, RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int ytiles = ny / ty;
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
     k_step2d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out, int nx,
-                 int ny, int rb, int cy, StepCoef<float> k, RunConst<float> rc, unsigned int* err)
+                 int ny, int rb, int cy, KickF k, RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Tile2D T{phi_in, phi_out, v, v_out, nx, ny, rb, (int)blockIdx.x * cy, 0};
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
     T.zn = min(cz, nz - T.z0);
     unsigned* wq = reinterpret_cast<unsigned*>(smem_raw + tile_smem3d(nx, ty)) + (threadIdx.x >> 5) * kQueuePerWarp;
     SiteAcc a{0.0, 0.0, 0.0f, 0.0f, 0, 0, 0, 0};
-    StepCoef<float> k{};
+    KickF k{};
     tile3d<ITEMS, false, true>(T, k, rc, smem_raw, wq, a, err);  // on a timeout the partial sums still reduce
     block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
 }
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
     T.yn = min(cy, ny - T.y0);
     unsigned* wq = reinterpret_cast<unsigned*>(smem_raw + tile_smem2d(nx, rb)) + (threadIdx.x >> 5) * kQueuePerWarp;
     SiteAcc a{0.0, 0.0, 0.0f, 0.0f, 0, 0, 0, 0};
-    StepCoef<float> k{};
+    KickF k{};
     tile2d<ITEMS, false, true>(T, k, rc, smem_raw, wq, a, err);
     block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
 }
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
     k_step_measure3d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out,
-                         int nx, int ny, int nz, int ty, int cz, StepCoef<float> k, RunConst<float> rc,
+                         int nx, int ny, int nz, int ty, int cz, KickF k, RunConst<float> rc,
                          DiagScratch scr, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
 template <int ITEMS>
 __global__ void __launch_bounds__(kFastThreads, 2)
     k_step_measure2d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out,
-                         int nx, int ny, int rb, int cy, StepCoef<float> k, RunConst<float> rc, DiagScratch scr,
+                         int nx, int ny, int rb, int cy, KickF k, RunConst<float> rc, DiagScratch scr,
                          unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -150,7 +150,7 @@ static int pick_chunks(int tiles, int len, int min_len, int slots, long long max
 }
 
 cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
-                             StepCoef<float> k, RunConst<float> rc, unsigned int* err, cudaStream_t st)
+                             KickF k, RunConst<float> rc, unsigned int* err, cudaStream_t st)
 {
     static std::atomic<unsigned long long> attr3{0}, attr2{0};
     const int t = kItems * 1024 / g.nx;
@@ -225,7 +225,7 @@ cudaError_t launch_measure_fast(const Geo& g, const float* phi, const float* v, 
 }
 
 cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
-                                     StepCoef<float> k, RunConst<float> rc, const DiagScratch& scr, unsigned int* err,
+                                     KickF k, RunConst<float> rc, const DiagScratch& scr, unsigned int* err,
                                      cudaStream_t st)
 {
     static std::atomic<unsigned long long> attr3{0}, attr2{0};

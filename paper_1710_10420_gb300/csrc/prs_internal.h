@@ -24,6 +24,16 @@ struct StepCoef {
     R c1, c2, cV;
 };
 
+// FP32 kick of one step (Eq. 4 with Eq. 6 and the force prefactor), the step's
+// constants folded:
+//   dphi' = c1 dphi + g s2 + phi (k1 - k2 phi^2),   s2 = sum of the 2D neighbours,
+// with g = c2/dx^2, k1 = c2 cV - 2D g and k2 = c2 cV/phi0^2, which is
+// c1 dphi + c2 (Lphi - cV phi (phi^2/phi0^2 - 1)) rearranged.  Computed in FP64 on the
+// host and rounded once (kick_f32).
+struct KickF {
+    float c1, g, k1, k2;
+};
+
 // Scalars fixed for the whole run, in working precision.
 template <typename R>
 struct RunConst {
@@ -69,6 +79,10 @@ struct DebugCheck {
     unsigned long long nonfinite; // non-finite values in phi^n and dphi
 };
 
+// The FP32 kick of a step from its coefficients (c1, c2, cV) and the run's constants
+// (the layout of RunConst: deta, 1/dx^2, 1/phi0^2, 2D, V0, phi0).
+KickF kick_f32(const double coef[3], const double run_const[6]);
+
 // Kernel launchers (prs_kernels.cu).  Each returns cudaSuccess or the launch error.
 cudaError_t launch_init_random(const Geo& g, int precision, uint64_t seed, void* phi, void* dphi, bool zero_dphi,
                                cudaStream_t st);
@@ -99,7 +113,7 @@ cudaError_t launch_measure_fast(const Geo& g, const float* phi, const float* v, 
 // One step (in -> out, v -> v_out) and the diagnostics of (in, v); cudaErrorNotSupported
 // when this box has no fused kernel.
 cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
-                                     StepCoef<float> k, RunConst<float> rc, const DiagScratch& scr, unsigned int* err,
+                                     KickF k, RunConst<float> rc, const DiagScratch& scr, unsigned int* err,
                                      cudaStream_t st);
 
 // Two fused leapfrog steps per pass (prs_tblock.cu), FP32 3D and 2D; dphi out of place.
@@ -107,7 +121,7 @@ bool tblock_ok(const Geo& g, int precision);
 // Rows of y per tile of the 3D two-step pass (0 when it does not apply).
 int tblock3_rows(const Geo& g);
 cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
-                           StepCoef<float> k0, StepCoef<float> k1, RunConst<float> rc, unsigned int* err,
+                           KickF k0, KickF k1, RunConst<float> rc, unsigned int* err,
                            cudaStream_t st);
 
 // Store a message for prs_last_error() on this thread.

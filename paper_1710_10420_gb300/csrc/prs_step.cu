@@ -6,7 +6,14 @@ namespace prs {
 cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const void* in, void* out, const void* dphi,
                                 void* dphi_out, double c1, double c2, double cV, const double rcd[6], cudaStream_t st);
 cudaError_t launch_step_fast(const Geo& g, const float* in, float* out, const float* v, float* v_out,
-                             StepCoef<float> k, RunConst<float> rc, unsigned int* err, cudaStream_t st);
+                             KickF k, RunConst<float> rc, unsigned int* err, cudaStream_t st);
+
+KickF kick_f32(const double coef[3], const double run_const[6])
+{
+    const double g = coef[1] * run_const[1];
+    const double h = coef[1] * coef[2];
+    return KickF{(float)coef[0], (float)g, (float)(h - run_const[3] * g), (float)(h * run_const[2])};
+}
 
 // Steps one pass may fuse (params.tblock above this is clamped).
 int max_fused_steps(const Geo& g, int precision, bool repro)
@@ -45,7 +52,8 @@ cudaError_t launch_step_io(const Geo& g, int precision, bool repro, const void* 
 {
     if (nsteps_in_pass != 1) return cudaErrorInvalidValue;
     if (fast_step_ok(g, precision)) {
-        StepCoef<float> k{(float)c1[0], (float)c2[0], (float)cV[0]};
+        const double coef[3] = {c1[0], c2[0], cV[0]};
+        const KickF k = kick_f32(coef, run_const);
         RunConst<float> rc{(float)run_const[0], (float)run_const[1], (float)run_const[2], (float)run_const[3],
                            (float)run_const[4], (float)run_const[5]};
         return launch_step_fast(g, (const float*)phi_in, (float*)phi_out, (const float*)dphi_in, (float*)dphi_out, k,

@@ -34,28 +34,31 @@ namespace {
 
 constexpr int kTbThreads = 320;  // at most; a CTA has ceil((ty+2) * xw/4 / kTbItems) threads
 constexpr int kTbItems = 2;      // level-1 float4 per thread per plane
-constexpr int kTbMaxTy = 14;     // 2 (ty+2) halo columns per plane, one lane each of warp 0
+constexpr int kTbMaxTy = 14;     // sliced tiles: 2 (ty+2) halo columns per plane, one lane each of warp 0
 
 static __device__ __noinline__ void drain4(uint64_t* bar, int from, int issued, unsigned int* err)
 {
     for (int i = from; i <= issued; ++i) mbar_wait(&bar[i & 3], (unsigned)(i >> 2) & 1u, err);
 }
 
-template <int ITEMS>
+template <int ITEMS, int XW, int TY>
 __global__ void __launch_bounds__(kTbThreads, 2)
     k_step3d_t2(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
-                float* __restrict__ v_out, int nx, int ny, int nz, int xw, int ty, int cz, StepCoef<float> k0,
-                StepCoef<float> k1, RunConst<float> rc, unsigned int* err)
+                float* __restrict__ v_out, int nx, int ny, int nz, int ty_, int cz, KickF k0,
+                KickF k1, RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    const int W = xw + 8;                  // floats per staged row: columns x0-4 .. x0+xw+3
+    constexpr int xw = XW;
+    constexpr int W = xw + 8;              // floats per staged row: columns x0-4 .. x0+xw+3
+    const int ty = TY > 0 ? TY : ty_;
     const int r0 = ty + 4, r1 = ty + 2;    // rows of a level-0 and a level-1 plane tile
     const int s0 = r0 * W, s1 = r1 * W;    // floats per ring slot
     float* ring0 = reinterpret_cast<float*>(smem_raw + 128);  // phi^n: 4 slots
     float* ring1 = ring0 + 4 * s0;                            // level 1: 2 slots
     float* ringv = ring1 + 2 * s1;                            // dphi^{n-1/2}: 3 slots
-    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nthr = TY > 0 ? ((TY + 2) * (XW / 4) / ITEMS + 31) / 32 * 32 : (int)blockDim.x;
     const int nxt = nx / xw, ytiles = ny / ty;
     const int x0 = (blockIdx.x % nxt) * xw;
     const int y0 = (blockIdx.x / nxt % ytiles) * ty;
@@ -78,15 +81,17 @@ __global__ void __launch_bounds__(kTbThreads, 2)
     // Iteration i stages phi plane i+2 and, for the level-1 planes 1..zn+2, dphi plane
     // i+1, both counted on bar[(i+2) % 4] (phi planes 0 and 1 go first, alone).  A staged
     // row is [x0-4, x0+xw+4) modulo nx: at most three runs, each a multiple of 4 floats
-    // at a 16-byte boundary, at the same columns in every row.  Thread c < 3 (r0 + r1)
-    // owns run c % 3 of staged row c / 3 (phi rows first, then dphi rows) for the whole
-    // pass, so staging a plane costs each copying thread one instruction sequence; thread
-    // 0 arms the barrier with the bytes (copies landing before it leave the count
-    // negative, which holds the phase open).
+    // at a 16-byte boundary, at the same columns in every row.  Copy task c < 3 (r0 + r1)
+    // is run c % 3 of staged row c / 3 (phi rows first, then dphi rows); thread
+    // nthr-1-c owns it for the whole pass (the last warps, whose second item lies in the
+    // level-1 halo row and has no level-2 work), so staging a plane costs each copying
+    // thread one instruction sequence; thread 0 arms the barrier with the bytes (copies
+    // landing before it leave the count negative, which holds the phase open).
     int cp_len = 0, cp_src = 0, cp_dst = 0;  // floats; source offset within a plane
     bool cp_v = false;
     {
-        const int r = tid / 3, u = tid - 3 * (tid / 3);
+        const int c = nthr - 1 - tid;
+        const int r = c / 3, u = c - 3 * (c / 3);
         int x = x0 >= 4 ? x0 - 4 : x0 - 4 + nx, p = 0;
         for (int run = 0; run < u && p < W; ++run) {
             p += min(W - p, nx - x);
@@ -125,10 +130,10 @@ __global__ void __launch_bounds__(kTbThreads, 2)
         off[j] = row * W + 4 + 4 * col;  // in a level-1 or dphi slot; +W in a level-0 slot
         go[j] = (y0 - 1 + row) * nx + x0 + 4 * col;  // in a plane, for the output rows
     }
-    // Halo columns of a sliced tile: lane h < 2 r1 of warp 0 owns level-1 row h/2 at
-    // column x0-1 (h even) or x0+xw (h odd).
+    // Halo columns of a sliced tile: thread h < 2 r1 owns level-1 row h/2 at column
+    // x0-1 (h even) or x0+xw (h odd).
     const bool hal = !whole && tid < 2 * r1;
-    const int hoff = (lane >> 1) * W + ((lane & 1) ? xw + 4 : 3);  // in a level-1 or dphi slot
+    const int hoff = (tid >> 1) * W + ((tid & 1) ? xw + 4 : 3);  // in a level-1 or dphi slot
 
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 f0m[ITEMS], f0c[ITEMS];  // level 0 at planes j-1, j of the level-1 plane j
@@ -242,7 +247,7 @@ static __device__ __noinline__ void drain_rows(uint64_t* bar, int from, int issu
 template <int ITEMS>
 __global__ void __launch_bounds__(kTb2Threads, 1)
     k_step2d_t2(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
-                  float* __restrict__ v_out, int nx, int ny, int cy, StepCoef<float> k0, StepCoef<float> k1,
+                  float* __restrict__ v_out, int nx, int ny, int cy, KickF k0, KickF k1,
                   RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -421,7 +426,7 @@ int tblock3_rows(const Geo& g)
 }
 
 cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
-                           StepCoef<float> k0, StepCoef<float> k1, RunConst<float> rc, unsigned int* err,
+                           KickF k0, KickF k1, RunConst<float> rc, unsigned int* err,
                            cudaStream_t st)
 {
     if (g.dims == 2) {
@@ -445,16 +450,20 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
         }
         return cudaGetLastError();
     }
-    static std::atomic<unsigned long long> attr{0};
-    {
-        const cudaError_t e = smem_limit_once(attr, (const void*)k_step3d_t2<kTbItems>, (int)kTbSmemMax);
-        if (e != cudaSuccess) return e;
-    }
     Tile3 t;
     if (!plan3(g, &t)) return cudaErrorInvalidValue;
+    // the common tile (256 x 8) has its own instantiation with every size known
+    const void* fn = t.xw == 256 ? (t.ty == 8 ? (const void*)k_step3d_t2<kTbItems, 256, 8>
+                                              : (const void*)k_step3d_t2<kTbItems, 256, 0>)
+                                 : (const void*)k_step3d_t2<kTbItems, 128, 0>;
+    static std::atomic<unsigned long long> attr[3];
+    {
+        const int which = t.xw == 256 ? (t.ty == 8 ? 0 : 1) : 2;
+        const cudaError_t e = smem_limit_once(attr[which], fn, (int)kTbSmemMax);
+        if (e != cudaSuccess) return e;
+    }
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_step3d_t2<kTbItems>, t.threads,
-                                                      t.smem) != cudaSuccess || per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, t.threads, t.smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
@@ -474,8 +483,15 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
     const int cz = (g.nz + best - 1) / best;
     const long long blocks = (long long)tiles * ((g.nz + cz - 1) / cz);
     if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
-    k_step3d_t2<kTbItems><<<(unsigned)blocks, t.threads, t.smem, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, g.nz,
-                                                                       t.xw, t.ty, cz, k0, k1, rc, err);
+    if (t.xw == 256 && t.ty == 8)
+        k_step3d_t2<kTbItems, 256, 8><<<(unsigned)blocks, t.threads, t.smem, st>>>(phi_in, phi_out, v_in, v_out, g.nx,
+                                                                                g.ny, g.nz, t.ty, cz, k0, k1, rc, err);
+    else if (t.xw == 256)
+        k_step3d_t2<kTbItems, 256, 0><<<(unsigned)blocks, t.threads, t.smem, st>>>(phi_in, phi_out, v_in, v_out, g.nx,
+                                                                                g.ny, g.nz, t.ty, cz, k0, k1, rc, err);
+    else
+        k_step3d_t2<kTbItems, 128, 0><<<(unsigned)blocks, t.threads, t.smem, st>>>(phi_in, phi_out, v_in, v_out, g.nx,
+                                                                                g.ny, g.nz, t.ty, cz, k0, k1, rc, err);
     return cudaGetLastError();
 }
 

@@ -32,31 +32,25 @@ __device__ __forceinline__ float4 ldg_stream4(const float* p) { return __ldcs(re
 __device__ __forceinline__ void stg4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
 // Eqs. 3-5 at one site, FP32: x neighbours (xp, xm), y neighbours (a, b), z neighbours
-// (e, f; 3D only).  Returns phi^{n+1}; vv becomes dphi^{n+1/2}.  The kick folds the
-// step's constants: with g = c2/dx^2 and h = c2 cV,
-//   dphi' = c1 dphi + g s2 + phi (h - 2D g - (h/phi0^2) phi^2),   s2 = sum of neighbours,
-// which is c1 dphi + c2 (Lphi - cV phi (phi^2/phi0^2 - 1)) rearranged: 11 operations a
-// site instead of 15 (the FP64 path keeps the canonical order of Eq. 3-5 as written).
-// Every term is odd in phi, so a negated field steps to the negated field exactly.
+// (e, f; 3D only).  Returns phi^{n+1}; vv becomes dphi^{n+1/2}.  The kick is KickF's
+// folded form, 11 operations a site (the FP64 path keeps the canonical order of Eqs. 3-5
+// as written); every term is odd in phi, so a negated field steps to the negated field
+// exactly.
 __device__ __forceinline__ float update1(float cc, float xp, float xm, float a, float b, float e, float f, float& vv,
-                                         const StepCoef<float>& k, const RunConst<float>& rc, bool three_d)
+                                         const KickF& k, const RunConst<float>& rc, bool three_d)
 {
-    const float g = k.c2 * rc.inv_dx2;
-    const float h = k.c2 * k.cV;
-    const float k1 = h - rc.twoD * g;
-    const float k2 = h * rc.inv_phi0sq;
     float s2 = xp + xm;
     s2 = s2 + (a + b);
     if (three_d) s2 = s2 + (e + f);
-    const float u = cc * (k1 - k2 * (cc * cc));
-    const float vn = k.c1 * vv + (g * s2 + u);
+    const float u = cc * (k.k1 - k.k2 * (cc * cc));
+    const float vn = k.c1 * vv + (k.g * s2 + u);
     vv = vn;
     return cc + rc.deta * vn;
 }
 
 // Eqs. 3-5 for the four sites of one float4.
 __device__ __forceinline__ void update4(float4 c, float left, float right, float4 yp, float4 ym, float4 zp, float4 zm,
-                                        float4& v, float4& pn, const StepCoef<float>& k, const RunConst<float>& rc,
+                                        float4& v, float4& pn, const KickF& k, const RunConst<float>& rc,
                                         bool three_d)
 {
     pn.x = update1(c.x, c.y, left, yp.x, ym.x, zp.x, zm.x, v.x, k, rc, three_d);
@@ -294,7 +288,7 @@ __host__ __device__ constexpr size_t tile_smem2d(int nx, int rb) { return 128 + 
 // One 3D tile: STEP applies Eqs. 3-5 (phi_in -> phi_out, v_in -> v_out); MEAS adds
 // the Eq. 7/8 terms of (phi_in, v_in) to `a`.  wq: this warp's link queue (MEAS).
 template <int ITEMS, bool STEP, bool MEAS>
-__device__ __forceinline__ bool tile3d(const Tile3D& T, const StepCoef<float>& k, const RunConst<float>& rc,
+__device__ __forceinline__ bool tile3d(const Tile3D& T, const KickF& k, const RunConst<float>& rc,
                                        unsigned char* smem, unsigned* wq, SiteAcc& a, unsigned int* err)
 {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -430,7 +424,7 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const StepCoef<float>& k
 // One 2D tile of row bands (rb = ITEMS*1024/nx rows each); slot i&3 of the ring
 // holds band i of the tile (band 0 = the row above it, band nb+1 = the row below).
 template <int ITEMS, bool STEP, bool MEAS>
-__device__ __forceinline__ bool tile2d(const Tile2D& T, const StepCoef<float>& k, const RunConst<float>& rc,
+__device__ __forceinline__ bool tile2d(const Tile2D& T, const KickF& k, const RunConst<float>& rc,
                                        unsigned char* smem, unsigned* wq, SiteAcc& a, unsigned int* err)
 {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
