@@ -726,18 +726,43 @@ static int prs_adjoint_impl(prs_sim* s, int64_t nsteps, int observable, double e
     } while (0)
 
     DiagScratch scr = s->scr;
+    // Fill the states k_from+1 .. k_to (slot(k): phi of state k, dphi at + fs) from state
+    // k_from, step n_first + k_from onwards: in pairs through the two-step pass, which
+    // also stores the state between its two steps (FP32 3D boxes it takes, without
+    // PRS_REPRO: 24 bytes a site per two states against 32), else one step at a time.
+    const bool pairs_ok = s->p.precision == PRS_FP32 && !repro && s->g.dims == 3 && tblock_ok(s->g, PRS_FP32);
+    const RunConst<float> rcf{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
+                              (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
+    auto fill = [&](auto slot, int64_t n_first, int64_t k_from, int64_t k_to) -> cudaError_t {
+        for (int64_t k = k_from; k < k_to;) {
+            double c0[5], c1[5];
+            step_coefficients(s->p, n_first + k, c0);
+            cudaError_t e;
+            if (pairs_ok && k + 2 <= k_to) {
+                step_coefficients(s->p, n_first + k + 1, c1);
+                char* x = slot(k);
+                char* y = slot(k + 1);
+                char* z = slot(k + 2);
+                e = launch_step_t2(s->g, (const float*)x, (float*)z, (const float*)(x + fs), (float*)(z + fs),
+                                   kick_f32(c0, s->rc), kick_f32(c1, s->rc), rcf, err, st, (float*)y,
+                                   (float*)(y + fs));
+                k += 2;
+            } else {
+                char* x = slot(k);
+                char* y = slot(k + 1);
+                e = launch_step_io(s->g, s->p.precision, repro, x, y, x + fs, y + fs, &c0[0], &c0[1], &c0[2], 1,
+                                   s->rc, err, st);
+                k += 1;
+            }
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     if (keep_all) {
         // forward, writing every state straight into its slot
         PRS_TRY(cudaMemcpyAsync(ckpt, s->phi[s->cur], fbytes, cudaMemcpyDeviceToDevice, st));
         PRS_TRY(cudaMemcpyAsync(ckpt + fs, s->dphi, fbytes, cudaMemcpyDeviceToDevice, st));
-        for (int64_t k = 0; k < nsteps; ++k) {
-            double c[5];
-            step_coefficients(s->p, n0 + k, c);
-            char* a = ckpt + 2 * fs * (size_t)k;
-            char* b = a + 2 * fs;
-            PRS_TRY(launch_step_io(s->g, s->p.precision, repro, a, b, a + fs, b + fs, &c[0], &c[1], &c[2], 1, s->rc,
-                                   err, st));
-        }
+        PRS_TRY(fill([&](int64_t k) { return ckpt + 2 * fs * (size_t)k; }, n0, 0, nsteps));
         char* last = ckpt + 2 * fs * (size_t)nsteps;
         PRS_TRY(cudaMemcpyAsync(s->phi[s->cur], last, fbytes, cudaMemcpyDeviceToDevice, st));
         PRS_TRY(cudaMemcpyAsync(s->dphi, last + fs, fbytes, cudaMemcpyDeviceToDevice, st));
@@ -759,14 +784,8 @@ static int prs_adjoint_impl(prs_sim* s, int64_t nsteps, int observable, double e
     for (int64_t i = nseg - 1; i >= 0; --i) {
         const int64_t a = n0 + i * K;
         const int64_t len = (i + 1) * K <= nsteps ? K : nsteps - i * K;
-        if (!keep_all) {
-            for (int64_t k = 0; k + 1 < len; ++k) {  // recompute states a+1 .. a+len-1
-                double c[5];
-                step_coefficients(s->p, a + k, c);
-                PRS_TRY(launch_step_io(s->g, s->p.precision, repro, state(k, i), state(k + 1, i), state(k, i) + fs,
-                                       state(k + 1, i) + fs, &c[0], &c[1], &c[2], 1, s->rc, err, st));
-            }
-        }
+        if (!keep_all)  // recompute states a+1 .. a+len-1
+            PRS_TRY(fill([&](int64_t k) { return state(k, i); }, a, 0, len - 1));
         for (int64_t k = len - 1; k >= 0; --k) {
             double c[5];
             step_coefficients(s->p, a + k, c);

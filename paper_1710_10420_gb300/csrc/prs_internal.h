@@ -120,9 +120,11 @@ cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, 
 bool tblock_ok(const Geo& g, int precision);
 // Rows of y per tile of the 3D two-step pass (0 when it does not apply).
 int tblock3_rows(const Geo& g);
+// phi_mid, v_mid (3D only; both or neither): also store the state between the two
+// steps there (cudaErrorNotSupported in 2D).
 cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
-                           KickF k0, KickF k1, RunConst<float> rc, unsigned int* err,
-                           cudaStream_t st);
+                           KickF k0, KickF k1, RunConst<float> rc, unsigned int* err, cudaStream_t st,
+                           float* phi_mid = nullptr, float* v_mid = nullptr);
 
 // Store a message for prs_last_error() on this thread.
 void record_error(const char* msg);

@@ -41,11 +41,13 @@ static __device__ __noinline__ void drain4(uint64_t* bar, int from, int issued, 
     for (int i = from; i <= issued; ++i) mbar_wait(&bar[i & 3], (unsigned)(i >> 2) & 1u, err);
 }
 
-template <int ITEMS, int XW, int TY>
+// MID: also store the state between the two steps (phi^{n+1}, dphi^{n+1/2}: level 1 at
+// the output sites) into phi_mid, v_mid.
+template <int ITEMS, int XW, int TY, bool MID>
 __global__ void __launch_bounds__(kTbThreads, 2)
     k_step3d_t2(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
-                float* __restrict__ v_out, int nx, int ny, int nz, int ty_, int cz, KickF k0,
-                KickF k1, RunConst<float> rc, unsigned int* err)
+                float* __restrict__ v_out, float* __restrict__ phi_mid, float* __restrict__ v_mid, int nx, int ny,
+                int nz, int ty_, int cz, KickF k0, KickF k1, RunConst<float> rc, unsigned int* err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -204,6 +206,10 @@ __global__ void __launch_bounds__(kTbThreads, 2)
                 if (lane == 31) right = c1p[4];
                 float4 pn;
                 float4 vv = w1[q];
+                if (MID) {
+                    stg4(phi_mid + zo + go[q], c);
+                    stg4(v_mid + zo + go[q], vv);
+                }
                 update4(c, left, right, lds4(c1p + W), lds4(c1p - W), f1p[q], f1m[q], vv, pn, k1, rc, true);
                 stg4(phi_out + zo + go[q], pn);
                 stg4(v_out + zo + go[q], vv);
@@ -408,54 +414,16 @@ bool plan3(const Geo& g, Tile3* t)
     return t->smem <= kTbSmemMax;
 }
 
-}  // namespace
-
-
-bool tblock_ok(const Geo& g, int precision)
+template <bool MID>
+cudaError_t launch3(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out, float* phi_mid,
+                    float* v_mid, KickF k0, KickF k1, RunConst<float> rc, unsigned int* err, cudaStream_t st)
 {
-    if (precision != PRS_FP32 || g.nx % 128 != 0) return false;
-    if (g.dims == 2) return g.nx <= 2 * kTb2Threads * 4;  // at most two float4 per thread of a row
-    Tile3 t;
-    return plan3(g, &t);
-}
-
-int tblock3_rows(const Geo& g)
-{
-    Tile3 t;
-    return g.dims == 3 && plan3(g, &t) ? t.ty : 0;
-}
-
-cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
-                           KickF k0, KickF k1, RunConst<float> rc, unsigned int* err,
-                           cudaStream_t st)
-{
-    if (g.dims == 2) {
-        static std::atomic<unsigned long long> attr1{0}, attr2{0};
-        const size_t sm = smem2d_t2(g.nx);
-        const int sms = sm_count_current();
-        const int cy = (g.ny + sms - 1) / sms;
-        const int blocks = (g.ny + cy - 1) / cy;
-        if (g.nx / 4 > kTb2Threads) {
-            const cudaError_t e =
-                smem_limit_once(attr2, (const void*)k_step2d_t2<2>, (int)smem2d_t2(8 * kTb2Threads));
-            if (e != cudaSuccess) return e;
-            k_step2d_t2<2><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
-                                                            rc, err);
-        } else {
-            const cudaError_t e =
-                smem_limit_once(attr1, (const void*)k_step2d_t2<1>, (int)smem2d_t2(4 * kTb2Threads));
-            if (e != cudaSuccess) return e;
-            k_step2d_t2<1><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
-                                                            rc, err);
-        }
-        return cudaGetLastError();
-    }
     Tile3 t;
     if (!plan3(g, &t)) return cudaErrorInvalidValue;
     // the common tile (256 x 8) has its own instantiation with every size known
-    const void* fn = t.xw == 256 ? (t.ty == 8 ? (const void*)k_step3d_t2<kTbItems, 256, 8>
-                                              : (const void*)k_step3d_t2<kTbItems, 256, 0>)
-                                 : (const void*)k_step3d_t2<kTbItems, 128, 0>;
+    const void* fn = t.xw == 256 ? (t.ty == 8 ? (const void*)k_step3d_t2<kTbItems, 256, 8, MID>
+                                              : (const void*)k_step3d_t2<kTbItems, 256, 0, MID>)
+                                 : (const void*)k_step3d_t2<kTbItems, 128, 0, MID>;
     static std::atomic<unsigned long long> attr[3];
     {
         const int which = t.xw == 256 ? (t.ty == 8 ? 0 : 1) : 2;
@@ -484,15 +452,63 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
     const long long blocks = (long long)tiles * ((g.nz + cz - 1) / cz);
     if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
     if (t.xw == 256 && t.ty == 8)
-        k_step3d_t2<kTbItems, 256, 8><<<(unsigned)blocks, t.threads, t.smem, st>>>(phi_in, phi_out, v_in, v_out, g.nx,
-                                                                                g.ny, g.nz, t.ty, cz, k0, k1, rc, err);
+        k_step3d_t2<kTbItems, 256, 8, MID><<<(unsigned)blocks, t.threads, t.smem, st>>>(
+            phi_in, phi_out, v_in, v_out, phi_mid, v_mid, g.nx, g.ny, g.nz, t.ty, cz, k0, k1, rc, err);
     else if (t.xw == 256)
-        k_step3d_t2<kTbItems, 256, 0><<<(unsigned)blocks, t.threads, t.smem, st>>>(phi_in, phi_out, v_in, v_out, g.nx,
-                                                                                g.ny, g.nz, t.ty, cz, k0, k1, rc, err);
+        k_step3d_t2<kTbItems, 256, 0, MID><<<(unsigned)blocks, t.threads, t.smem, st>>>(
+            phi_in, phi_out, v_in, v_out, phi_mid, v_mid, g.nx, g.ny, g.nz, t.ty, cz, k0, k1, rc, err);
     else
-        k_step3d_t2<kTbItems, 128, 0><<<(unsigned)blocks, t.threads, t.smem, st>>>(phi_in, phi_out, v_in, v_out, g.nx,
-                                                                                g.ny, g.nz, t.ty, cz, k0, k1, rc, err);
+        k_step3d_t2<kTbItems, 128, 0, MID><<<(unsigned)blocks, t.threads, t.smem, st>>>(
+            phi_in, phi_out, v_in, v_out, phi_mid, v_mid, g.nx, g.ny, g.nz, t.ty, cz, k0, k1, rc, err);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+
+bool tblock_ok(const Geo& g, int precision)
+{
+    if (precision != PRS_FP32 || g.nx % 128 != 0) return false;
+    if (g.dims == 2) return g.nx <= 2 * kTb2Threads * 4;  // at most two float4 per thread of a row
+    Tile3 t;
+    return plan3(g, &t);
+}
+
+int tblock3_rows(const Geo& g)
+{
+    Tile3 t;
+    return g.dims == 3 && plan3(g, &t) ? t.ty : 0;
+}
+
+cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
+                           KickF k0, KickF k1, RunConst<float> rc, unsigned int* err, cudaStream_t st,
+                           float* phi_mid, float* v_mid)
+{
+    if (g.dims == 2) {
+        if (phi_mid || v_mid) return cudaErrorNotSupported;
+        static std::atomic<unsigned long long> attr1{0}, attr2{0};
+        const size_t sm = smem2d_t2(g.nx);
+        const int sms = sm_count_current();
+        const int cy = (g.ny + sms - 1) / sms;
+        const int blocks = (g.ny + cy - 1) / cy;
+        if (g.nx / 4 > kTb2Threads) {
+            const cudaError_t e =
+                smem_limit_once(attr2, (const void*)k_step2d_t2<2>, (int)smem2d_t2(8 * kTb2Threads));
+            if (e != cudaSuccess) return e;
+            k_step2d_t2<2><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
+                                                            rc, err);
+        } else {
+            const cudaError_t e =
+                smem_limit_once(attr1, (const void*)k_step2d_t2<1>, (int)smem2d_t2(4 * kTb2Threads));
+            if (e != cudaSuccess) return e;
+            k_step2d_t2<1><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
+                                                            rc, err);
+        }
+        return cudaGetLastError();
+    }
+    if ((phi_mid == nullptr) != (v_mid == nullptr)) return cudaErrorInvalidValue;
+    if (phi_mid) return launch3<true>(g, phi_in, phi_out, v_in, v_out, phi_mid, v_mid, k0, k1, rc, err, st);
+    return launch3<false>(g, phi_in, phi_out, v_in, v_out, nullptr, nullptr, k0, k1, rc, err, st);
 }
 
 }  // namespace prs
