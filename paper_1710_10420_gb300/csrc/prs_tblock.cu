@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(kTbThreads, 2)
     float* ring1 = ring0 + 4 * s0;                            // level 1: 2 slots
     float* ringv = ring1 + 2 * s1;                            // dphi^{n-1/2}: 3 slots
     const int tid = threadIdx.x, lane = tid & 31;
-    const int nthr = TY > 0 ? ((TY + 2) * (XW / 4) / ITEMS + 31) / 32 * 32 : (int)blockDim.x;
+    // the launch's thread count (plan3's formula), a constant for a fixed tile shape
+    const int nthr = TY > 0 ? (((TY + 2) * (XW / 4) + ITEMS - 1) / ITEMS + 31) / 32 * 32 : (int)blockDim.x;
     const int nxt = nx / xw, ytiles = ny / ty;
     const int x0 = (blockIdx.x % nxt) * xw;
     const int y0 = (blockIdx.x / nxt % ytiles) * ty;
