@@ -251,12 +251,14 @@ static __device__ __noinline__ void drain_rows(uint64_t* bar, int from, int issu
     for (int i = from; i <= issued; ++i) mbar_wait(&bar[i % kR2Slots0], (i / kR2Slots0) & 1, err);
 }
 
-template <int ITEMS>
+// NX > 0: the row width as a compile-time constant (the 4096-wide production box).
+template <int ITEMS, int NX>
 __global__ void __launch_bounds__(kTb2Threads, 1)
     k_step2d_t2(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
-                  float* __restrict__ v_out, int nx, int ny, int cy, KickF k0, KickF k1,
+                  float* __restrict__ v_out, int nx_, int ny, int cy, KickF k0, KickF k1,
                   RunConst<float> rc, unsigned int* err)
 {
+    const int nx = NX > 0 ? NX : nx_;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* ring0 = reinterpret_cast<float*>(smem_raw + 128);
@@ -494,15 +496,22 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
         const int blocks = (g.ny + cy - 1) / cy;
         if (g.nx / 4 > kTb2Threads) {
             const cudaError_t e =
-                smem_limit_once(attr2, (const void*)k_step2d_t2<2>, (int)smem2d_t2(8 * kTb2Threads));
+                smem_limit_once(attr2, (const void*)k_step2d_t2<2, 0>, (int)smem2d_t2(8 * kTb2Threads));
             if (e != cudaSuccess) return e;
-            k_step2d_t2<2><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
-                                                            rc, err);
+            static std::atomic<unsigned long long> attr4{0};
+            const cudaError_t e4 = smem_limit_once(attr4, (const void*)k_step2d_t2<2, 4096>, (int)smem2d_t2(4096));
+            if (e4 != cudaSuccess) return e4;
+            if (g.nx == 4096)
+                k_step2d_t2<2, 4096><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0,
+                                                                      k1, rc, err);
+            else
+                k_step2d_t2<2, 0><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
+                                                                   rc, err);
         } else {
             const cudaError_t e =
-                smem_limit_once(attr1, (const void*)k_step2d_t2<1>, (int)smem2d_t2(4 * kTb2Threads));
+                smem_limit_once(attr1, (const void*)k_step2d_t2<1, 0>, (int)smem2d_t2(4 * kTb2Threads));
             if (e != cudaSuccess) return e;
-            k_step2d_t2<1><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
+            k_step2d_t2<1, 0><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
                                                             rc, err);
         }
         return cudaGetLastError();
