@@ -73,8 +73,9 @@ __global__ void __launch_bounds__(kFastThreads, 2)
     block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
 }
 
-// One leapfrog step and the diagnostics of its input state from one read of it.
-template <int ITEMS>
+// One leapfrog step and the diagnostics of its input state from one read of it (NX > 0:
+// an instantiation for that row width, the 1024-wide production box).
+template <int ITEMS, int NX>
 __global__ void __launch_bounds__(kFastThreads, 2)
     k_step_measure3d_f32(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* v, float* v_out,
                          int nx, int ny, int nz, int ty, int cz, KickF k, RunConst<float> rc,
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kFastThreads, 2)
     T.zn = min(cz, nz - T.z0);
     unsigned* wq = reinterpret_cast<unsigned*>(smem_raw + tile_smem3d(nx, ty)) + (threadIdx.x >> 5) * kQueuePerWarp;
     SiteAcc a{0.0, 0.0, 0.0f, 0.0f, 0, 0, 0, 0};
-    tile3d<ITEMS, true, true>(T, k, rc, smem_raw, wq, a, err);
+    tile3d<ITEMS, true, true, NX>(T, k, rc, smem_raw, wq, a, err);
     block_reduce_and_finish(DiagAcc{a.sw, a.sr, a.nl, a.nw, a.nv0, a.nnf}, scr);
 }
 
@@ -235,7 +236,10 @@ cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, 
         const size_t sm = smem3d(g.nx, t) + kQueueBytes;
         if (sm > kMeasureSmemMax) return cudaErrorNotSupported;
         {
-            const cudaError_t e = smem_limit_once(attr3, (const void*)k_step_measure3d_f32<kItems>, (int)kMeasureSmemMax);
+            cudaError_t e = smem_limit_once(attr3, (const void*)k_step_measure3d_f32<kItems, 0>, (int)kMeasureSmemMax);
+            static std::atomic<unsigned long long> attr31{0};
+            if (e == cudaSuccess)
+                e = smem_limit_once(attr31, (const void*)k_step_measure3d_f32<kItems, 1024>, (int)kMeasureSmemMax);
             if (e != cudaSuccess) return e;
         }
         const int ytiles = g.ny / t;
@@ -244,8 +248,12 @@ cudaError_t launch_step_measure_fast(const Geo& g, const float* in, float* out, 
         const int cz = (g.nz + nchunks - 1) / nchunks;
         nchunks = (g.nz + cz - 1) / cz;
         if ((long long)ytiles * nchunks > scr.max_blocks) return cudaErrorNotSupported;
-        k_step_measure3d_f32<kItems><<<ytiles * nchunks, kFastThreads, sm, st>>>(in, out, v, v_out, g.nx, g.ny, g.nz,
-                                                                                 t, cz, k, rc, scr, err);
+        if (g.nx == 1024)
+            k_step_measure3d_f32<kItems, 1024><<<ytiles * nchunks, kFastThreads, sm, st>>>(
+                in, out, v, v_out, g.nx, g.ny, g.nz, t, cz, k, rc, scr, err);
+        else
+            k_step_measure3d_f32<kItems, 0><<<ytiles * nchunks, kFastThreads, sm, st>>>(
+                in, out, v, v_out, g.nx, g.ny, g.nz, t, cz, k, rc, scr, err);
         return cudaGetLastError();
     }
     const size_t sm = smem2d(g.nx, t) + kQueueBytes;

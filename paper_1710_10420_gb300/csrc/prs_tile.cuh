@@ -287,14 +287,16 @@ __host__ __device__ constexpr size_t tile_smem2d(int nx, int rb) { return 128 + 
 
 // One 3D tile: STEP applies Eqs. 3-5 (phi_in -> phi_out, v_in -> v_out); MEAS adds
 // the Eq. 7/8 terms of (phi_in, v_in) to `a`.  wq: this warp's link queue (MEAS).
-template <int ITEMS, bool STEP, bool MEAS>
+// NX > 0: the row width as a compile-time constant (then ty = ITEMS * 1024 / NX).
+template <int ITEMS, bool STEP, bool MEAS, int NX = 0>
 __device__ __forceinline__ bool tile3d(const Tile3D& T, const KickF& k, const RunConst<float>& rc,
                                        unsigned char* smem, unsigned* wq, SiteAcc& a, unsigned int* err)
 {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     float* ring = reinterpret_cast<float*>(smem + 128);
     const int tid = threadIdx.x, lane = tid & 31;
-    const int nx = T.nx, ny = T.ny, nz = T.nz, ty = T.ty, y0 = T.y0, z0 = T.z0, zn = T.zn;
+    const int nx = NX > 0 ? NX : T.nx, ty = NX > 0 ? ITEMS * 1024 / NX : T.ty;
+    const int ny = T.ny, nz = T.nz, y0 = T.y0, z0 = T.z0, zn = T.zn;
     const int nq = nx >> 2;
     const double rscale = MEAS && rc.V0 > 0.0f ? 1.0 / (double)rc.V0 : 0.0;  // see wall_sites4
     const int tile = (ty + 2) * nx;
