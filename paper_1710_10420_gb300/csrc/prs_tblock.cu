@@ -17,8 +17,8 @@
 // and y neighbours: each thread keeps the values of its own columns at planes z-1, z,
 // z+1 in registers, for level 0 and for level 1, so one barrier per plane suffices.
 // Level 1 also computes the two columns just outside a sliced tile (x0-1 and x0+xw,
-// one lane per row and side), which level 2 needs as x neighbours; for whole rows those
-// are the row's own wrapped end columns.  dphi enters level 1 on ty+2 rows (its halo
+// one thread of warp 0 per row and side), which level 2 needs as x neighbours; for
+// whole rows those are the row's own wrapped end columns.  dphi enters level 1 on ty+2 rows (its halo
 // rows belong to neighbouring tiles), so it is read from one buffer and written to
 // another; the level-1 dphi stays in the registers of the thread that owns its site
 // until level 2 uses it.
@@ -414,7 +414,8 @@ bool plan3(const Geo& g, Tile3* t)
     t->ty = ty;
     t->threads = (((ty + 2) * nq + kTbItems - 1) / kTbItems + 31) / 32 * 32;
     t->smem = 128 + (size_t)(4 * (ty + 4) + 5 * (ty + 2)) * (xw + 8) * sizeof(float);
-    return t->smem <= kTbSmemMax;
+    // one thread per copy task (3 runs of each of the 2 ty + 6 staged rows)
+    return t->smem <= kTbSmemMax && t->threads >= 3 * (2 * ty + 6);
 }
 
 template <bool MID>
