@@ -264,6 +264,26 @@ def traffic_record(workload: str, tblock: int):
     return rec
 
 
+def library_split(nsteps: int, tb: int):
+    """(two-step passes, single steps) of prs_step(nsteps) with tb steps per pass: the
+    library runs pairs, and after an odd number of pairs one single step brings dphi back to
+    the run's own buffer, so with an even step count an odd number of pairs gives up one pair."""
+    pairs = nsteps // 2 if tb == 2 else 0
+    if pairs % 2 and nsteps == 2 * pairs:
+        pairs -= 1
+    return pairs, nsteps - 2 * pairs
+
+
+def interval_calls(rest: int, tb: int):
+    """The plain steps of an output interval as two calls (pure, tail) with the same passes as
+    prs_step(rest): `pure` steps that are all passes of the step kernel (with two steps per
+    pass an even number of pairs, which the library splits no further), then the remaining
+    `tail`; events bracket them, so the first bracket times the step kernel alone."""
+    pairs, _ = library_split(rest, tb)
+    pure = 2 * (pairs - pairs % 2) if tb == 2 else rest
+    return pure, rest - pure
+
+
 def run_gpu(args, world, rank, local):
     import torch
 
@@ -282,17 +302,9 @@ def run_gpu(args, world, rank, local):
     # fused into its first leapfrog step (prs_step_measure), then the other interval-1
     # steps (prs_step)
     rest = args.interval - 1
-    pairs = rest // 2 if tb == 2 else 0  # the library's split of prs_step(rest) into passes
-    if pairs % 2 and rest == 2 * pairs:
-        pairs -= 1
-    singles = rest - 2 * pairs
+    pairs, singles = library_split(rest, tb)
     step_launches = pairs + singles
-    # the rest runs as two calls with the same passes as prs_step(rest): first `pure` steps
-    # that are all passes of the step kernel (with two steps per pass an even number of
-    # pairs, which the library splits no further), then the remaining `tail`; events
-    # bracket the three calls, so the middle bracket times the step kernel alone
-    pure = 2 * (pairs - pairs % 2) if tb == 2 else rest
-    tail = rest - pure
+    pure, tail = interval_calls(rest, tb)
     pure_launches = pure // tb
 
     def one_step(events=None):

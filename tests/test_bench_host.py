@@ -59,6 +59,22 @@ def test_clock_summary(bench):
     assert c.summary()["reasons"] == ["unsampled"]
 
 
+def test_interval_calls_keep_the_library_passes(bench):
+    """The benchmark's two calls per interval run exactly the passes of one prs_step(rest), and
+    the first call holds only launches of the step kernel."""
+    for tb in (1, 2):
+        for rest in range(0, 64):
+            pure, tail = bench.interval_calls(rest, tb)
+            assert pure + tail == rest and pure >= 0 and tail >= 0
+            p_all, s_all = bench.library_split(rest, tb)
+            p_pure, s_pure = bench.library_split(pure, tb)
+            p_tail, s_tail = bench.library_split(tail, tb)
+            assert (p_pure + p_tail, s_pure + s_tail) == (p_all, s_all), (tb, rest)
+            assert s_pure == 0 if tb == 2 else p_pure == 0
+            assert p_pure % 2 == 0  # dphi is back in the run's own buffer after the first call
+    assert bench.interval_calls(19, 2) == (16, 3) and bench.library_split(19, 2) == (9, 1)
+
+
 def test_kernel_source_hash_and_traffic_record(bench):
     h = bench.kernel_sources_sha()
     assert len(h) == 16 and h == bench.kernel_sources_sha()
