@@ -246,9 +246,11 @@ def test_measure_tiny_magnitudes(shape):
 
 
 @pytest.mark.parametrize("precision,shape", [(prs.PRS_FP32, (256, 64, 40)), (prs.PRS_FP32, (512, 96)),
-                                             (prs.PRS_FP32, (37, 23)), (prs.PRS_FP64, (32, 24, 16))])
+                                             (prs.PRS_FP32, (1024, 16, 12)), (prs.PRS_FP32, (37, 23)),
+                                             (prs.PRS_FP64, (32, 24, 16))])
 def test_step_measure_fused(precision, shape):
-    """prs_step_measure = prs_measure_ex of the start state, then prs_step: same numbers, same field."""
+    """prs_step_measure = prs_measure_ex of the start state, then prs_step: same numbers, same field
+    (1024-wide 3D rows: the fused pass's instantiation for that width)."""
     a = prs.Sim(shape, precision=precision, seed=9)
     b = prs.Sim(shape, precision=precision, seed=9)
     a.init().step(7)
