@@ -382,7 +382,7 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": desc, "shape": list(shape), "interval": args.interval,
                    "diagnostics": "of the state at the start of each interval, fused into its first step",
                    "fused_steps_per_pass": tb,
-                   "l2": "inputs larger than L2 (state 12 GB)" if sites >= 512 ** 3 else
+                   "l2": "inputs larger than L2 (state 16 GB: phi, phi', dphi and the second dphi buffer of two-step passes)" if sites >= 512 ** 3 else
                    "state comparable to L2; not flushed", "parallelism": f"replicas x{world}",
                    "last_output": {"area_per_volume": d.area_per_volume, "gamma_v": d.gamma_v, "step": d.step}},
         "roofline": roofline, "e2e": e2e, "clocks": clocks,
