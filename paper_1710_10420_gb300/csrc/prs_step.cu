@@ -24,12 +24,12 @@ int max_fused_steps(const Geo& g, int precision, bool repro)
 
 // The library's default number of steps per pass.  FP32 3D: two wherever the two-step
 // pass gets tiles of at least 4 rows (fewer rows make level 1 recompute more than it
-// saves) — per step against one step per pass, measured 14.5 against 22.1 us at 128^3,
-// 46.3 against 49.1 us at 256^3, 0.269 against 0.323 ms at 512^3 and 1.96 against 2.53 ms
+// saves) — per step against one step per pass, measured 13.6 against 22.7 us at 128^3,
+// 38.2 against 48.2 us at 256^3, 0.230 against 0.323 ms at 512^3 and 1.67 against 2.53 ms
 // at 1024^3.  FP32 2D: two once the state (three fields) outgrows L2 — rows are
-// whole, so level 1 recomputes only the two rows outside each chunk (4096^2: 28 us
-// against 48 us per step); an L2-resident state (2048^2) steps faster one step at a
-// time.  FP64 and other boxes: one.
+// whole, so level 1 recomputes only the two rows outside each chunk (4096^2: 26 us
+// against 48 us per step); an L2-resident state (2048^2) steps about as fast one step at a
+// time (10.6 against 10.4 us).  FP64 and other boxes: one.
 int default_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)repro;
