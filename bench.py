@@ -373,6 +373,7 @@ def run_gpu(args, world, rank, local):
     if rec:
         roofline["dram_frac"] = rec["dram_bytes_per_launch"] / (launch_avg_ms / 1e3) / 1e9 / peak
 
+    state_gb = sites * 4 * (4 if tb == 2 else 3) / 1e9  # FP32 fields resident on the device
     e2e = run_e2e(args, prs, sim, shape, stream, dev, world)
     clocks = clk.summary()
     line = {
@@ -382,8 +383,9 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": desc, "shape": list(shape), "interval": args.interval,
                    "diagnostics": "of the state at the start of each interval, fused into its first step",
                    "fused_steps_per_pass": tb,
-                   "l2": "inputs larger than L2 (state 16 GB: phi, phi', dphi and the second dphi buffer of two-step passes)" if sites >= 512 ** 3 else
-                   "state comparable to L2; not flushed", "parallelism": f"replicas x{world}",
+                   "l2": (f"inputs larger than L2 (state {state_gb:.1f} GB: phi, phi', dphi"
+                          + (" and the second dphi buffer of two-step passes)" if tb == 2 else ")"))
+                   if sites >= 512 ** 3 else "state comparable to L2; not flushed", "parallelism": f"replicas x{world}",
                    "last_output": {"area_per_volume": d.area_per_volume, "gamma_v": d.gamma_v, "step": d.step}},
         "roofline": roofline, "e2e": e2e, "clocks": clocks,
         "gpu_launches": args.steps * (step_launches + 1),  # one fused step+diagnostics launch per interval
