@@ -36,6 +36,9 @@ WORKLOADS = {
     "2d4096": ((4096, 4096), "2D 4096^2 FP32 PRS step (5-point), radiation era, 20 steps + FP64 wall diagnostics"),
 }
 BYTES_PER_SITE_UPDATE = {0: 16, 1: 32}  # read+write of phi and dphi (FP32, FP64)
+# one metric string for both arms, so that their values can be compared
+METRIC = "PRS site-updates/s (FP32) and % HBM roofline"
+REPEATS = 5  # the timed region is also reported as the median of this many equal repeats
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
@@ -55,6 +58,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward time figure")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64 rate and FP32-vs-FP64 figure")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D 4096^2 figure")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) figure")
     ap.add_argument("--no-table1", action="store_true", help="skip the scaling-exponent (Table I) figure")
     ap.add_argument("--adjoint-steps", type=int, default=1270, help="leapfrog steps of the adjoint figure")
     ap.add_argument("--batch-scale", type=float, default=1.0,
@@ -207,12 +211,13 @@ def run_reference(args, world, rank):
         secs += s
     value = units / secs
     line = {
-        "impl": "reference", "metric": "PRS site-updates/s (FP64 oracle on host cores)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "site-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][1], "reference_sample": "3D 64^3 FP64 oracle per step",
-                   "interval": args.interval},
+                   "interval": args.interval,
+                   "reference": "the FP64 CPU oracle (no reference implementation exists), single-threaded"},
         "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
                          "sample": f"3D 64^3, {args.interval} leapfrog steps + diagnostics per step"},
         "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -348,6 +353,18 @@ def run_gpu(args, world, rank, local):
     else:  # an interval too short for a pure bracket: the plain passes' mean
         launch_avg_ms = tail_ms / max(step_launches, 1)
     value = aggregate(sites * args.interval * args.steps, world, ms_max / 1e3)
+    # the same timed region as REPEATS equal repeats of consecutive intervals (event pairs
+    # per interval, so no extra synchronisation inside the region): their rates and median
+    per_interval = [e[0].elapsed_time(e[3]) for e in events]
+    reps = []
+    size = max(1, len(per_interval) // REPEATS)
+    for r in range(min(REPEATS, len(per_interval))):
+        chunk = per_interval[r * size:(r + 1) * size] if r < REPEATS - 1 else per_interval[r * size:]
+        reps.append(sites * args.interval * len(chunk) / (sum(chunk) / 1e3))
+    repeats = {"n": len(reps), "values": reps, "median": statistics.median(reps) if reps else None,
+               "unit": "site-updates/s",
+               "note": f"the {args.steps} timed intervals split into {len(reps)} consecutive repeats, each timed "
+                       "by the CUDA events that bracket its intervals"}
 
     peak, peak_kind = peaks()
     # algorithmic bytes of one pass: phi^n and dphi read once, phi and dphi written once,
@@ -374,11 +391,15 @@ def run_gpu(args, world, rank, local):
         roofline["dram_frac"] = rec["dram_bytes_per_launch"] / (launch_avg_ms / 1e3) / 1e9 / peak
 
     state_gb = sites * 4 * (4 if tb == 2 else 3) / 1e9  # FP32 fields resident on the device
-    e2e = run_e2e(args, prs, sim, shape, stream, dev, world)
+    e2e = None if args.no_e2e else run_e2e(args, prs, sim, shape, stream, dev, world)
     clocks = clk.summary()
     line = {
-        "metric": "PRS site-updates/s (FP32) and % HBM roofline", "value": value, "unit": "site-updates/s",
+        "metric": METRIC, "value": value, "unit": "site-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "ms_per_leapfrog_step": ms_max / (args.steps * args.interval),
+        "step_means": f"one bench step = one output interval of {args.interval} leapfrog steps with the "
+                      "diagnostics of its start state",
+        "repeats": repeats,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "shape": list(shape), "interval": args.interval,
                    "diagnostics": "of the state at the start of each interval, fused into its first step",
@@ -503,25 +524,27 @@ def run_batch_figure(prs, stream, dev, scale: float) -> dict:
     tl = {f"{s[0]}^{len(s)}": prs.prs_batch_tuning(b, k)[0] for k, (s, *_r) in enumerate(runs)}
     budget = prs.prs_batch_tuning(b, 0)[1]
     prs.prs_batch_destroy(b)
-    # one run at a time: prs_step between outputs, prs_measure at each output
+    # one run at a time, with the library's fastest single-run path: each output interval is one
+    # prs_step_measure (the diagnostics of its start state fused into its first pass), and the
+    # state after the last interval is measured by prs_measure_ex when it falls on an output
     a.record(stream)
     for (s, m, sd, n) in runs:
         sim = prs.Sim(s, stream=stream, device=dev, era_m=m, seed=sd)
         sim.init()
         done = 0
-        prs.prs_measure_ex(sim.handle)
         while done < n:
             k = min(every, n - done)
-            prs.prs_step(sim.handle, k)
+            prs.prs_step_measure(sim.handle, k)
             done += k
-            if done % every == 0:
-                prs.prs_measure_ex(sim.handle)
+        if done % every == 0:
+            prs.prs_measure_ex(sim.handle)
         sim.close()
     z.record(stream)
     torch.cuda.synchronize(dev)
     ms_seq = a.elapsed_time(z)
     return {"workload": "16 x 2D 256^2, 16 x 1024^2, 16 x 2048^2 and 16 x 3D 128^3, FP32, each to eta = N/2"
                         + ("" if scale == 1.0 else f" x {scale} of the steps") + ", diagnostics every 20 steps",
+            "one_at_a_time": "prs_step_measure(20) per output interval, one run after another",
             "site_updates": total, "batched_s": ms_batch / 1e3, "one_at_a_time_s": ms_seq / 1e3,
             "batched_value": total / (ms_batch / 1e3), "one_at_a_time_value": total / (ms_seq / 1e3),
             "unit": "site-updates/s", "speedup": ms_seq / ms_batch, "create_s": t_create,

@@ -151,11 +151,22 @@ int prs_bind(prs_sim* sim, void* d_phi_a, void* d_phi_b, void* d_dphi);
 int prs_init(prs_sim* sim, const void* h_phi, const void* h_dphi);
 
 /* Queue nsteps (>= 0) leapfrog steps (Eqs. 3-6) on the run's stream; returns
- * without waiting.  Step n uses delta_n, eta_n = eta0 + n deta.  Passes of two
- * steps (see prs_params.tblock) write dphi out of place: the first call that makes
- * them allocates a second dphi buffer, owned by the run and freed by prs_destroy (if
- * that allocation fails, the steps run one per pass).  dphi always ends in the run's
- * own buffer. */
+ * without waiting (the call never allocates, so it may be captured into a CUDA graph).
+ * Step n uses delta_n, eta_n = eta0 + n deta.  Every step of the call must satisfy the
+ * stability limit (checked at both ends, where the force prefactor a^beta is largest),
+ * else PRS_EINVAL.  Passes of two steps (see prs_params.tblock) read dphi across sites
+ * and write it out of place, into a second dphi buffer that prs_init, prs_set_state or
+ * prs_set_state_device allocate when the run takes two-step passes (owned by the run,
+ * freed by prs_destroy; if that allocation fails, the steps run one per pass).
+ * Where dphi ends:
+ *   - library-owned buffers (no prs_bind, no PRS_DEBUG): after an odd number of
+ *     two-step passes the two dphi buffers swap roles; every step count keeps all its
+ *     pairs.  prs_device_state returns the current buffer.
+ *   - bound buffers (prs_bind) or PRS_DEBUG: dphi ends in the run's own buffer after
+ *     every call.  An odd step count keeps all its pairs (the last single step brings
+ *     dphi home); an even count whose pairs are odd in number (2, 6, 10, ...) runs one
+ *     pair as two single steps, so a caller stepping by a multiple of 4 (or an odd count)
+ *     gets only two-step passes. */
 int prs_step(prs_sim* sim, int64_t nsteps);
 
 /* Wall diagnostics of the current state (Eq. 7, Eq. 8), reduced on the device in
@@ -191,8 +202,16 @@ int prs_set_state(prs_sim* sim, const void* h_phi, const void* h_dphi, int64_t n
  * run steps; from pageable memory CUDA may complete them before returning. */
 int prs_set_state_async(prs_sim* sim, const void* h_phi, const void* h_dphi, int64_t n);
 
+/* As prs_set_state, from device arrays (both required; current device, the run's
+ * layout and precision): the copies are queued on the run's stream without waiting, so
+ * the arrays must stay valid and unchanged until the stream has passed them, and work
+ * that produced them on another stream must be ordered before the call (e.g. by an
+ * event).  A source that already is the run's current buffer is left in place. */
+int prs_set_state_device(prs_sim* sim, const void* d_phi, const void* d_dphi, int64_t n);
+
 /* Device pointers of the current fields and the step index (any output may be
- * NULL).  The pointers stay valid until the next prs_step or prs_destroy. */
+ * NULL).  The pointers stay valid until the next prs_step or prs_destroy (a run with
+ * library-owned buffers may hold dphi in either of its two dphi buffers). */
 int prs_device_state(prs_sim* sim, void** d_phi, void** d_dphi, int64_t* n);
 
 /* Wall diagnostics without any device allocation.  The paper has no counterpart:
@@ -205,8 +224,9 @@ int prs_device_state(prs_sim* sim, void** d_phi, void** d_dphi, int64_t* n);
  * memory on every GPU that loads it, kept until the process exits.  Limit:
  * 2^30 sites (1024^3); larger lattices return PRS_EINVAL (see prs_last_error).
  * The first call on a device looks up that array's address with the device
- * current (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  Every call shares the one array, which keeps the last call's
+ * current (cudaGetSymbolAddress) and caches it for the life of the process; make
+ * that first call before any stream capture, and do not call this entry point after
+ * a cudaDeviceReset (the cached address would be stale).  Every call shares the one array, which keeps the last call's
  * contents (the call clears what must start at zero), so calls that overlap on
  * the GPU, from several streams or threads, race: serialise them.  Synchronises
  * `stream`.  out->step is -1 and out->eta 0: the fields carry no step index. */

@@ -113,6 +113,7 @@ _SIGS = {
     "prs_get_state": (ctypes.c_int, [_VP, _VP, _VP, _I64P]),
     "prs_set_state": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64]),
     "prs_set_state_async": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64]),
+    "prs_set_state_device": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64]),
     "prs_device_state": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I64P]),
     "prs_destroy": (ctypes.c_int, [_VP]),
     "prs_coefficients": (ctypes.c_int, [_P, ctypes.c_int64, _DP]),
@@ -238,6 +239,13 @@ def prs_get_state(sim, h_phi=None, h_dphi=None) -> int:
 
 def prs_set_state(sim, h_phi, h_dphi, n: int) -> None:
     _check(load().prs_set_state(sim, _ptr(h_phi), _ptr(h_dphi), n), "prs_set_state")
+
+
+def prs_set_state_device(sim, d_phi, d_dphi, n: int) -> None:
+    """Device-to-device state copy, queued on the run's stream (torch tensors or raw pointers)."""
+    p = d_phi if isinstance(d_phi, int) else _ptr(d_phi)
+    v = d_dphi if isinstance(d_dphi, int) else _ptr(d_dphi)
+    _check(load().prs_set_state_device(sim, p, v, n), "prs_set_state_device")
 
 
 def prs_set_state_async(sim, h_phi, h_dphi, n: int) -> None:
@@ -426,8 +434,12 @@ def observable_with_grad(shape, phi_init, v_init, nsteps, observable, eps_smooth
     class _PRSObservable(torch.autograd.Function):
         @staticmethod
         def forward(ctx, phi0, v0, alpha):
-            sim = Sim(shape, precision=precision, alpha=float(alpha.item()), **kw)
-            sim.set_state(phi0.detach().cpu().numpy(), v0.detach().cpu().numpy(), 0)
+            sim = Sim(shape, precision=precision, alpha=float(alpha.item()), device=phi0.device, **kw)
+            # device to device, on the run's stream (the caller's current stream)
+            phi_c = phi0.detach().to(sim.dtype).contiguous()
+            v_c = v0.detach().to(device=phi0.device, dtype=sim.dtype).contiguous()
+            sim.stream.wait_stream(torch.cuda.current_stream(phi0.device))
+            prs_set_state_device(sim.handle, phi_c, v_c, 0)
             gphi = torch.empty_like(phi0)
             gv = torch.empty_like(v0)
             J, dA = prs_adjoint(sim.handle, nsteps, observable, eps_smooth, ckpt_every, gphi, gv)

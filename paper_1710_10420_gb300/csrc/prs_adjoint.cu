@@ -669,7 +669,7 @@ static int prs_adjoint_impl(prs_sim* s, int64_t nsteps, int observable, double e
     if (observable != PRS_OBS_GRAD_ENERGY && observable != PRS_OBS_SMOOTH_AREA) return PRS_EINVAL;
     if (observable == PRS_OBS_SMOOTH_AREA && !(eps_smooth > 0)) return PRS_EINVAL;
     if (!s->initialised) return PRS_ESTATE;
-    if (nsteps > 0 && !cfl_ok(s->p, s->n + nsteps - 1)) return PRS_EINVAL;
+    if (nsteps > 0 && !cfl_ok_over(s->p, s->n, nsteps)) return PRS_EINVAL;
     const size_t fbytes = (size_t)s->g.S * s->elem;
     const int64_t n0 = s->n;
     const bool repro = (s->p.flags & PRS_REPRO) != 0;

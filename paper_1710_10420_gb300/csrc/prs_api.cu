@@ -248,6 +248,29 @@ extern "C" int prs_destroy(prs_sim* s)
 
 // ------------------------------------------------------------------ state
 
+// Steps per pass this run takes (params.tblock, or the library's choice, clamped).
+static int run_tblock(const prs_sim* s)
+{
+    const bool repro = (s->p.flags & PRS_REPRO) != 0;
+    int tmax = max_fused_steps(s->g, s->p.precision, repro);
+    int tb = s->p.tblock > 0 ? s->p.tblock : default_fused_steps(s->g, s->p.precision, repro);
+    if (tb > tmax) tb = tmax;
+    return tb < 1 ? 1 : tb;
+}
+
+// The second dphi buffer of two-step passes, allocated with the fields (prs_init,
+// prs_set_state) so that prs_step itself never allocates; if there is no room the run
+// steps one step per pass.
+static void ensure_dphi_alt(prs_sim* s)
+{
+    if (s->dphi_alt || run_tblock(s) < 2) return;
+    if (cudaMalloc(&s->dphi_alt, (size_t)s->g.S * s->elem) != cudaSuccess) {
+        cudaGetLastError();
+        s->dphi_alt = nullptr;
+    }
+}
+
+
 static int prs_init_impl(prs_sim* s, const void* h_phi, const void* h_dphi)
 {
     if (!s) return PRS_EINVAL;
@@ -268,6 +291,7 @@ static int prs_init_impl(prs_sim* s, const void* h_phi, const void* h_dphi)
     }
     // host arrays may be pageable and reused by the caller right after return
     PRS_CUDA(cudaStreamSynchronize(s->stream));
+    ensure_dphi_alt(s);
     s->n = 0;
     s->initialised = true;
     return PRS_OK;
@@ -282,6 +306,7 @@ static int set_state_queued(prs_sim* s, const void* h_phi, const void* h_dphi, i
     PRS_CUDA(cudaMemcpyAsync(s->phi[s->cur], h_phi, bytes, cudaMemcpyHostToDevice, s->stream));
     PRS_CUDA(cudaMemcpyAsync(s->dphi, h_dphi, bytes, cudaMemcpyHostToDevice, s->stream));
     if (wait) PRS_CUDA(cudaStreamSynchronize(s->stream));
+    ensure_dphi_alt(s);
     s->n = n;
     s->initialised = true;
     return PRS_OK;
@@ -295,6 +320,26 @@ static int prs_set_state_impl(prs_sim* s, const void* h_phi, const void* h_dphi,
 extern "C" int prs_set_state_async(prs_sim* s, const void* h_phi, const void* h_dphi, int64_t n)
 {
     return debug_after(s, set_state_queued(s, h_phi, h_dphi, n, false), "prs_set_state_async", true);
+}
+
+static int set_state_device(prs_sim* s, const void* d_phi, const void* d_dphi, int64_t n)
+{
+    if (!s || !d_phi || !d_dphi || n < 0) return PRS_EINVAL;
+    int rc = ensure_buffers(s);
+    if (rc) return rc;
+    size_t bytes = (size_t)s->g.S * s->elem;
+    if (d_phi != s->phi[s->cur])
+        PRS_CUDA(cudaMemcpyAsync(s->phi[s->cur], d_phi, bytes, cudaMemcpyDeviceToDevice, s->stream));
+    if (d_dphi != s->dphi) PRS_CUDA(cudaMemcpyAsync(s->dphi, d_dphi, bytes, cudaMemcpyDeviceToDevice, s->stream));
+    ensure_dphi_alt(s);
+    s->n = n;
+    s->initialised = true;
+    return PRS_OK;
+}
+
+extern "C" int prs_set_state_device(prs_sim* s, const void* d_phi, const void* d_dphi, int64_t n)
+{
+    return debug_after(s, set_state_device(s, d_phi, d_dphi, n), "prs_set_state_device", true);
 }
 
 extern "C" int prs_get_state(prs_sim* s, void* h_phi, void* h_dphi, int64_t* n)
@@ -352,32 +397,33 @@ cudaError_t prs::smem_limit_once(std::atomic<unsigned long long>& done, const vo
 
 // ------------------------------------------------------------------- step
 
+bool prs::cfl_ok_over(const prs_params& p, int64_t n, int64_t nsteps)
+{
+    return cfl_ok(p, n) && cfl_ok(p, n + nsteps - 1);
+}
+
 static int prs_step_impl(prs_sim* s, int64_t nsteps)
 {
     if (!s || nsteps < 0) return PRS_EINVAL;
     if (!s->initialised) return PRS_ESTATE;
     if (nsteps == 0) return PRS_OK;
-    if (!cfl_ok(s->p, s->n + nsteps - 1)) return PRS_EINVAL;
+    if (!cfl_ok_over(s->p, s->n, nsteps)) return PRS_EINVAL;
     const bool repro = (s->p.flags & PRS_REPRO) != 0;
-    int tmax = max_fused_steps(s->g, s->p.precision, repro);
-    int tb = s->p.tblock > 0 ? s->p.tblock : default_fused_steps(s->g, s->p.precision, repro);
-    if (tb > tmax) tb = tmax;
-    if (tb < 1) tb = 1;
+    const int tb = run_tblock(s);
     // Two-step passes read dphi across sites, so they write it to a second buffer.
-    // After an odd number of them dphi sits in that buffer: the single step after
-    // them reads it there and writes the run's own buffer, so an odd step count keeps
-    // every pair; with an even count and an odd number of pairs, one pair runs as two
-    // single steps instead.  Single steps otherwise update dphi in place.
+    // After an odd number of them dphi sits in that buffer.  A run whose buffers the
+    // library owns (no PRS_DEBUG guard bands) then just swaps the roles of its two dphi
+    // buffers.  A run with bound buffers keeps dphi in the bound buffer at the end of
+    // every call: the single step after an odd number of pairs reads dphi in the second
+    // buffer and writes the bound one, so an odd step count keeps every pair; with an
+    // even count and an odd number of pairs, one pair runs as two single steps instead.
+    // Single steps otherwise update dphi in place.
+    const bool swap_ok = s->owned && (s->p.flags & PRS_DEBUG) == 0;
     int64_t pairs = tb == 2 ? nsteps / 2 : 0;
-    if ((pairs & 1) && nsteps == 2 * pairs) --pairs;
-    if (pairs > 0 && !s->dphi_alt) {
-        if (cudaMalloc(&s->dphi_alt, (size_t)s->g.S * s->elem) != cudaSuccess) {
-            cudaGetLastError();
-            s->dphi_alt = nullptr;
-            pairs = 0;  // no room for the second buffer: single steps
-        }
-    }
+    if ((pairs & 1) && nsteps == 2 * pairs && !swap_ok) --pairs;
+    if (pairs > 0 && !s->dphi_alt) pairs = 0;  // no second buffer (no room at prs_init): single steps
     const int64_t singles = nsteps - 2 * pairs;
+    const bool swap_home = (pairs & 1) && singles == 0;  // only when swap_ok
     unsigned int* err = &s->d_status->error;
     const RunConst<float> rcf{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
                               (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
@@ -401,6 +447,11 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
                                        s->dphi, &c[0], &c[1], &c[2], 1, s->rc, err, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
         s->cur = 1 - s->cur;
+    }
+    if (swap_home) {  // dphi now sits in the second buffer, which becomes the run's own
+        void* t = s->dphi;
+        s->dphi = s->dphi_alt;
+        s->dphi_alt = t;
     }
     s->n += nsteps;
     return PRS_OK;
@@ -481,7 +532,7 @@ static int prs_step_measure_impl(prs_sim* s, int64_t nsteps, prs_diag* out)
     if (!s || !out || nsteps < 0) return PRS_EINVAL;
     if (!s->initialised) return PRS_ESTATE;
     if (nsteps == 0) return measure_into(s, out);
-    if (!cfl_ok(s->p, s->n + nsteps - 1)) return PRS_EINVAL;
+    if (!cfl_ok_over(s->p, s->n, nsteps)) return PRS_EINVAL;
     const int64_t n0 = s->n;
     cudaError_t e = cudaErrorNotSupported;
     if (fast_diag_ok(s)) {

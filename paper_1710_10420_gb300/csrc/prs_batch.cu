@@ -637,7 +637,7 @@ extern "C" int prs_batch_run(prs_batch* b, const int64_t* nsteps_per_run, int64_
     const int R = (int)b->p.size();
     for (int r = 0; r < R; ++r) {
         if (nsteps_per_run[r] < 0) return PRS_EINVAL;
-        if (nsteps_per_run[r] > 0 && !cfl_ok(b->p[r], b->n[r] + nsteps_per_run[r] - 1)) return PRS_EINVAL;
+        if (nsteps_per_run[r] > 0 && !cfl_ok_over(b->p[r], b->n[r], nsteps_per_run[r])) return PRS_EINVAL;
         if (measure_every > 0 && (!out_series || nsteps_per_run[r] / measure_every + 1 > out_capacity))
             return PRS_EINVAL;
     }

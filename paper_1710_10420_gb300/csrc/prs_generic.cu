@@ -302,7 +302,7 @@ static cudaError_t measure_grid_t(const Geo& g, const void* phi, const void* dph
 cudaError_t launch_measure_on_grid(const Geo& g, int precision, const void* phi, const void* dphi,
                                    const double rcd[6], const DiagScratch& scr, int grid, cudaStream_t st)
 {
-    if (grid < 1 || grid > scr.max_blocks) return cudaErrorInvalidValue;
+    if (grid < 1 || grid > scr.max_blocks || grid > 65535) return cudaErrorInvalidValue;  // gridDim.y limit
     if (precision == PRS_FP32) return measure_grid_t<float>(g, phi, dphi, rcd, scr, grid, st);
     return measure_grid_t<double>(g, phi, dphi, rcd, scr, grid, st);
 }

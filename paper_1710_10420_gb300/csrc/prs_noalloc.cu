@@ -35,6 +35,8 @@ static const size_t kScratchBytes = kCounterOffset + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+static const int64_t kMaxGridY = 65535;  // CUDA's limit on gridDim.y
+
 static const int kMaxDevices = 64;
 static std::mutex g_setup_mutex;
 static void* g_scratch_addr[kMaxDevices];
@@ -110,7 +112,11 @@ extern "C" int prs_measure_noalloc(const prs_params* p, const void* d_phi, const
     double rcd[6] = {p->deta, 1.0 / (p->dx * p->dx), 1.0 / (p->phi0 * p->phi0), (double)(2 * p->dims),
                      pi * pi / (2.0 * p->W0 * p->W0), p->phi0};
     cudaStream_t st = (cudaStream_t)stream;
-    int grid = (int)((S + kNoAllocSitesPerBlock - 1) / kNoAllocSitesPerBlock);
+    // one block per kNoAllocSitesPerBlock sites, striding over the rows along gridDim.y,
+    // whose limit (65535) is one below the 65536 partial slots: at the 2^30-site limit the
+    // blocks take a few more rows each
+    int64_t want = (S + kNoAllocSitesPerBlock - 1) / kNoAllocSitesPerBlock;
+    const int grid = (int)(want < kMaxGridY ? want : kMaxGridY);
 
     // the completion counter must start at zero; a previous call normally leaves it
     // there, but an interrupted one might not

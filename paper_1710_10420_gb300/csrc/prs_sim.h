@@ -36,6 +36,10 @@ namespace prs {
 void step_coefficients(const prs_params& p, int64_t n, double out[5]);
 // Leapfrog stability at step n.
 bool cfl_ok(const prs_params& p, int64_t n);
+// Leapfrog stability at every step n .. n+nsteps-1 (nsteps >= 1): the force prefactor
+// cV ~ a^beta = eta^(m beta) is monotonic in eta, so its largest value over the steps is
+// at the first (beta < 0) or the last (beta > 0), and both ends are checked.
+bool cfl_ok_over(const prs_params& p, int64_t n, int64_t nsteps);
 // Record a CUDA error for prs_last_error(); returns PRS_ECUDA.
 int cuda_fail(cudaError_t e, const char* what);
 // Allocate the field buffers if none are bound or allocated yet.

@@ -75,8 +75,9 @@ def boosted_kink_pair(shape, W0: float, u: float, axis: int = 0):
     a = math.pi * g / W0
     A = np.tanh(a * (x - x1))
     B = -np.tanh(a * (x - x2))
-    dA = -u * a / np.cosh(a * (x - x1)) ** 2
-    dB = u * a / np.cosh(a * (x - x2)) ** 2
+    with np.errstate(over="ignore"):  # far from a wall cosh overflows and sech^2 is 0
+        dA = -u * a / np.cosh(a * (x - x1)) ** 2
+        dB = u * a / np.cosh(a * (x - x2)) ** 2
     return A * B, dA * B + A * dB
 
 

@@ -269,6 +269,32 @@ def test_step_measure_fused(precision, shape):
     assert _rel(pb, pa.astype(np.float64)) <= 1e-6 and _rel(vb, va.astype(np.float64)) <= 1e-6
 
 
+@pytest.mark.parametrize("shape", [(1024, 16, 12), (1024, 24, 16)])
+@pytest.mark.parametrize("field", ["random", "boosted"])
+def test_step_measure_1024_wide_vs_oracle(shape, field):
+    """The bench's fused step + diagnostics pass for 1024-wide 3D rows (Eqs. 3-5, 7, 8 from one
+    read of the state) against the oracle directly: exact counts, A/V and gamma v to 1e-5 on the
+    start state, then the fields after the following steps to 1e-5."""
+    if field == "random":
+        phi = inp.random_field(shape, 41).astype(np.float32)
+        v = (0.3 * inp.random_field(shape, 42)).astype(np.float32)
+    else:
+        phi, v = inp.boosted_kink_pair(shape, 6.0, 0.4, axis=0)
+        phi, v = phi.astype(np.float32), v.astype(np.float32)
+    sim = prs.Sim(shape, precision=prs.PRS_FP32, W0=6.0)
+    sim.set_state(phi, v, 0)
+    d = prs.prs_step_measure(sim.handle, 9)
+    pg, vg, n = sim.get_state()
+    sim.close()
+    p = oracle.Params(shape, W0=6.0)
+    od = oracle.measure(p, phi.astype(np.float64), v.astype(np.float64))
+    assert (d.n_links, d.n_wall, d.n_vzero, d.n_nonfinite) == (od.n_links, od.n_wall, od.n_vzero, od.n_nonfinite)
+    assert d.area_per_volume == pytest.approx(od.area_per_volume, rel=1e-5)
+    assert d.gamma_v == pytest.approx(od.gamma_v, rel=1e-5)
+    ophi, ov = oracle.step(p, phi.astype(np.float64), v.astype(np.float64), 9)
+    assert n == 9 and _rel(pg, ophi) <= 1e-5 and _rel(vg, ov) <= 1e-5
+
+
 def test_measure_nonfinite_and_empty():
     shape = (16, 16)
     sim = prs.Sim(shape, precision=prs.PRS_FP64)

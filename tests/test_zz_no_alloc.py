@@ -56,6 +56,23 @@ def test_noalloc_matches_measure_twice(precision, shape):
     sim.close()
 
 
+def test_noalloc_at_its_site_limit():
+    """2^30 sites (1024^3 FP32, the headline box), the documented maximum: the blocks
+    stride over the rows on a grid that stays within CUDA's gridDim.y limit."""
+    import torch
+
+    shape = (1024, 1024, 1024)
+    sim = _sim(shape, prs.PRS_FP32, seed=9, nsteps=3)
+    ref = prs.prs_measure_ex(sim.handle)
+    d_phi, d_dphi, _ = prs.prs_device_state(sim.handle)
+    for _ in range(2):
+        d = prs.prs_measure_noalloc(sim.params, d_phi, d_dphi, sim.stream.cuda_stream)
+        _check_same(d, ref, prs.PRS_FP32)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+
 def test_noalloc_alternating_runs():
     """The shared array keeps the previous call's contents; results must not depend on it."""
     a = _sim((128, 96), prs.PRS_FP32, seed=1, nsteps=10)
