@@ -126,6 +126,13 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
                            KickF k0, KickF k1, RunConst<float> rc, unsigned int* err, cudaStream_t st,
                            float* phi_mid = nullptr, float* v_mid = nullptr);
 
+// The two-step pass with TMA tensor copies (prs_t2tma.cu) for FP32 3D boxes tiled by 256 x 8
+// (cudaErrorNotSupported for other boxes, or when the tensor-map encoder is unavailable).
+bool t2tma_ok(const Geo& g);
+cudaError_t launch_step_t2_tma(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
+                               KickF k0, KickF k1, RunConst<float> rc, unsigned int* err, cudaStream_t st,
+                               float* phi_mid, float* v_mid);
+
 // Store a message for prs_last_error() on this thread.
 void record_error(const char* msg);
 

@@ -524,6 +524,10 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
         return cudaGetLastError();
     }
     if ((phi_mid == nullptr) != (v_mid == nullptr)) return cudaErrorInvalidValue;
+    if (t2tma_ok(g)) {  // the production tile: planes staged by tensor copies
+        const cudaError_t e = launch_step_t2_tma(g, phi_in, phi_out, v_in, v_out, k0, k1, rc, err, st, phi_mid, v_mid);
+        if (e != cudaErrorNotSupported) return e;
+    }
     if (phi_mid) return launch3<true>(g, phi_in, phi_out, v_in, v_out, phi_mid, v_mid, k0, k1, rc, err, st);
     return launch3<false>(g, phi_in, phi_out, v_in, v_out, nullptr, nullptr, k0, k1, rc, err, st);
 }

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "prs_internal.h"
+#include "prs_f32x2.cuh"
 #include "prs_ptx.cuh"
 
 namespace prs {
@@ -35,28 +36,46 @@ __device__ __forceinline__ void stg4(float* p, float4 v) { *reinterpret_cast<flo
 // (e, f; 3D only).  Returns phi^{n+1}; vv becomes dphi^{n+1/2}.  The kick is KickF's
 // folded form, 11 operations a site (the FP64 path keeps the canonical order of Eqs. 3-5
 // as written); every term is odd in phi, so a negated field steps to the negated field
-// exactly.
+// exactly.  Each operation is pinned (round-to-nearest intrinsics, the three fused
+// multiply-adds explicit), so update4's packed pairs give the same bits.
 __device__ __forceinline__ float update1(float cc, float xp, float xm, float a, float b, float e, float f, float& vv,
                                          const KickF& k, const RunConst<float>& rc, bool three_d)
 {
-    float s2 = xp + xm;
-    s2 = s2 + (a + b);
-    if (three_d) s2 = s2 + (e + f);
-    const float u = cc * (k.k1 - k.k2 * (cc * cc));
-    const float vn = k.c1 * vv + (k.g * s2 + u);
+    float s2 = __fadd_rn(xp, xm);
+    s2 = __fadd_rn(s2, __fadd_rn(a, b));
+    if (three_d) s2 = __fadd_rn(s2, __fadd_rn(e, f));
+    const float u = __fmul_rn(cc, __fmaf_rn(-k.k2, __fmul_rn(cc, cc), k.k1));
+    const float vn = __fmaf_rn(k.c1, vv, __fmaf_rn(k.g, s2, u));
     vv = vn;
-    return cc + rc.deta * vn;
+    return __fmaf_rn(rc.deta, vn, cc);
 }
 
-// Eqs. 3-5 for the four sites of one float4.
+// Eqs. 3-5 for the four sites of one float4: update1's operations on two packed pairs
+// of sites (x, y) and (z, w), one f32x2 instruction per pair and operation, except the
+// x-neighbour sums, whose operands straddle the pairs.
 __device__ __forceinline__ void update4(float4 c, float left, float right, float4 yp, float4 ym, float4 zp, float4 zm,
                                         float4& v, float4& pn, const KickF& k, const RunConst<float>& rc,
                                         bool three_d)
 {
-    pn.x = update1(c.x, c.y, left, yp.x, ym.x, zp.x, zm.x, v.x, k, rc, three_d);
-    pn.y = update1(c.y, c.z, c.x, yp.y, ym.y, zp.y, zm.y, v.y, k, rc, three_d);
-    pn.z = update1(c.z, c.w, c.y, yp.z, ym.z, zp.z, zm.z, v.z, k, rc, three_d);
-    pn.w = update1(c.w, right, c.z, yp.w, ym.w, zp.w, zm.w, v.w, k, rc, three_d);
+    const f2 kc1 = pk2(k.c1, k.c1), kg = pk2(k.g, k.g), kk1 = pk2(k.k1, k.k1), nk2 = pk2(-k.k2, -k.k2);
+    const f2 dt = pk2(rc.deta, rc.deta);
+    f2 s0 = pk2(__fadd_rn(c.y, left), __fadd_rn(c.z, c.x));
+    f2 s1 = pk2(__fadd_rn(c.w, c.y), __fadd_rn(right, c.z));
+    s0 = add2(s0, add2(pk2(yp.x, yp.y), pk2(ym.x, ym.y)));
+    s1 = add2(s1, add2(pk2(yp.z, yp.w), pk2(ym.z, ym.w)));
+    if (three_d) {
+        s0 = add2(s0, add2(pk2(zp.x, zp.y), pk2(zm.x, zm.y)));
+        s1 = add2(s1, add2(pk2(zp.z, zp.w), pk2(zm.z, zm.w)));
+    }
+    const f2 c0 = pk2(c.x, c.y), c1 = pk2(c.z, c.w);
+    const f2 u0 = mul2(c0, fma2(nk2, mul2(c0, c0), kk1));
+    const f2 u1 = mul2(c1, fma2(nk2, mul2(c1, c1), kk1));
+    const f2 v0 = fma2(kc1, pk2(v.x, v.y), fma2(kg, s0, u0));
+    const f2 v1 = fma2(kc1, pk2(v.z, v.w), fma2(kg, s1, u1));
+    upk2(v0, v.x, v.y);
+    upk2(v1, v.z, v.w);
+    upk2(fma2(dt, v0, c0), pn.x, pn.y);
+    upk2(fma2(dt, v1, c1), pn.z, pn.w);
 }
 
 // x-neighbours of a float4 at column `col` of a whole row in shared memory.
