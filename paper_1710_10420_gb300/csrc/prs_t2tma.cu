@@ -140,14 +140,15 @@ __device__ __forceinline__ void issue_plane(const Ctx& c, const T2Maps& m, int p
     }
 }
 
-// One plane iteration i of the march.  Queues: am, ac, ap = level 0 at planes j-1, j,
-// j+1 (ap is loaded here); bm, bc, bp = level 1 at planes k-1, k, k+1 (bp is computed
-// here); hm, hc, hp: the halo lane's level 0.  Returns false when a wait gave up.
+// One plane iteration i of the march.  Level 0 at planes j, j+1 and level 1 at plane k are
+// read from the rings (the stencil reads their x and y neighbours there anyway); only the
+// planes that have left the rings stay in registers: am = level 0 at plane j-1, bm = level
+// 1 at plane k-1, w1 = the level-1 dphi^{n+1/2} at plane k, and the halo lane's level 0 at
+// planes j-1, j (hm, hc).  Returns false when a wait gave up.
 template <bool MID>
 __device__ __forceinline__ bool plane_iter(const Ctx& c, const T2Maps& m, int i, int& issued, const KickF& k0,
                                            const KickF& k1, const RunConst<float>& rc, float4 (&am)[2],
-                                           float4 (&ac)[2], float4 (&ap)[2], float4 (&bm)[2], float4 (&bc)[2],
-                                           float4 (&bp)[2], float4 (&w1)[2], float& hm, float& hc, float& hp)
+                                           float4 (&bm)[2], float4 (&w1)[2], float& hm, float& hc)
 {
     const bool ok = mbar_wait(&c.bar[i & 3], (unsigned)(i >> 2) & 1u, c.err);
     if (__syncthreads_or(!ok)) {
@@ -162,43 +163,40 @@ __device__ __forceinline__ bool plane_iter(const Ctx& c, const T2Maps& m, int i,
     const int k = i - 2;  // level-2 plane of this iteration
     const float* Ln = c.ring0 + (i & 3) * kS0;        // level-0 plane j+1
     const float* Lj = c.ring0 + ((i + 3) & 3) * kS0;  // level-0 plane j
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        ap[h] = lds4(Ln + c.o0[h]);
-        bp[h] = z4;
-    }
-    hp = c.hal ? Ln[c.hc] : 0.f;
-    float4 w1n[2] = {z4, z4};
+    const float hp = c.hal ? Ln[c.hc] : 0.f;
+    float4 pn[2], w1n[2];  // level 1 at plane j (phi, dphi) of this thread's float4
     if (j >= 1 && j <= c.zn + 2) {
         float* L1 = c.ring1 + (j & 1) * kS1;
         const float* V = c.ringv + (j % 3) * kSV;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const float4 cc = ac[h];
+            const float4 cc = lds4(Lj + c.o0[h]);
             const float e = Lj[c.e0[h]];  // lane 0: the left neighbour, lane 31: the right one
             const float su = __shfl_up_sync(0xffffffffu, cc.w, 1), sd = __shfl_down_sync(0xffffffffu, cc.x, 1);
             const float left = c.lane == 0 ? e : su, right = c.lane == 31 ? e : sd;
-            float4 vv = lds4(V + c.o0[h] - kXW);  // dphi row = level-1 row
-            float4 pn;
-            update4(cc, left, right, lds4(Lj + c.o0[h] + kXW), lds4(Lj + c.o0[h] - kXW), ap[h], am[h], vv, pn, k0, rc,
-                    true);
-            *reinterpret_cast<float4*>(L1 + c.o1[h]) = pn;
-            bp[h] = pn;
-            w1n[h] = vv;
+            w1n[h] = lds4(V + c.o0[h] - kXW);  // dphi row = level-1 row
+            update4(cc, left, right, lds4(Lj + c.o0[h] + kXW), lds4(Lj + c.o0[h] - kXW), lds4(Ln + c.o0[h]), am[h],
+                    w1n[h], pn[h], k0, rc, true);
+            *reinterpret_cast<float4*>(L1 + c.o1[h]) = pn[h];
+            am[h] = cc;
         }
         if (c.hal) {
             float vv = V[c.hv];
             L1[c.ho] = update1(hc, Lj[c.hxp], Lj[c.hxm], Lj[c.hc + 4], Lj[c.hc - 4], hp, hm, vv, k0, rc, true);
         }
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) am[h] = lds4(Lj + c.o0[h]);
     }
+    hm = hc;
+    hc = hp;
     if (k >= 2 && k <= c.zn + 1) {
         const float* L1 = c.ring1 + (k & 1) * kS1;
         const size_t zo = (size_t)(c.z0 - 2 + k) * c.plane;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (h == 0 ? c.tid < 64 : c.tid >= 256) continue;  // the level-1 halo rows 0, 9 (warp-uniform)
-            const float4 cc = bc[h];
+            const float4 cc = lds4(L1 + c.o1[h]);
             const float e = L1[c.o1[h] + (c.lane == 0 ? -1 : 4)];
             const float su = __shfl_up_sync(0xffffffffu, cc.w, 1), sd = __shfl_down_sync(0xffffffffu, cc.x, 1);
             const float left = c.lane == 0 ? e : su, right = c.lane == 31 ? e : sd;
@@ -207,12 +205,17 @@ __device__ __forceinline__ bool plane_iter(const Ctx& c, const T2Maps& m, int i,
                 stg4(c.phi_mid + zo + c.go[h], cc);
                 stg4(c.v_mid + zo + c.go[h], vv);
             }
-            float4 pn;
-            update4(cc, left, right, lds4(L1 + c.o1[h] + kW1), lds4(L1 + c.o1[h] - kW1), bp[h], bm[h], vv, pn, k1, rc,
+            float4 out;
+            update4(cc, left, right, lds4(L1 + c.o1[h] + kW1), lds4(L1 + c.o1[h] - kW1), pn[h], bm[h], vv, out, k1, rc,
                     true);
-            stg4(c.phi_out + zo + c.go[h], pn);
+            stg4(c.phi_out + zo + c.go[h], out);
             stg4(c.v_out + zo + c.go[h], vv);
+            bm[h] = cc;
         }
+    } else if (k == 1) {  // level 1 at plane 1, the first level-2 plane's z neighbour below
+        const float* L1 = c.ring1 + kS1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) bm[h] = lds4(L1 + c.o1[h]);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) w1[h] = w1n[h];
@@ -297,23 +300,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     int issued = 1;
 
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 a0[2] = {z4, z4}, a1[2] = {z4, z4}, a2[2] = {z4, z4};
-    float4 b0[2] = {z4, z4}, b1[2] = {z4, z4}, b2[2] = {z4, z4};
-    float4 w1[2] = {z4, z4};
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    // (a0, a1, a2): level 0 at planes j-1, j, j+1; (b0, b1, b2): level 1 at k-1, k, k+1
-    for (int i = 0; i < c.nplanes; ++i) {
-        if (!plane_iter<MID>(c, maps, i, issued, k0, k1, rc, a0, a1, a2, b0, b1, b2, w1, g0, g1, g2)) return;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            a0[h] = a1[h];
-            a1[h] = a2[h];
-            b0[h] = b1[h];
-            b1[h] = b2[h];
-        }
-        g0 = g1;
-        g1 = g2;
-    }
+    float4 am[2] = {z4, z4}, bm[2] = {z4, z4}, w1[2] = {z4, z4};
+    float hm = 0.f, hc = 0.f;
+    for (int i = 0; i < c.nplanes; ++i)
+        if (!plane_iter<MID>(c, maps, i, issued, k0, k1, rc, am, bm, w1, hm, hc)) return;
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
