@@ -269,23 +269,28 @@ def traffic_record(workload: str, tblock: int):
     return rec
 
 
-def library_split(nsteps: int, tb: int):
-    """(two-step passes, single steps) of prs_step(nsteps) with tb steps per pass: the
-    library runs pairs, and after an odd number of pairs one single step brings dphi back to
-    the run's own buffer, so with an even step count an odd number of pairs gives up one pair."""
-    pairs = nsteps // 2 if tb == 2 else 0
-    if pairs % 2 and nsteps == 2 * pairs:
-        pairs -= 1
-    return pairs, nsteps - 2 * pairs
+class OwnedRun:
+    """A run whose fields the library allocates (prs_create without prs_bind): after an odd number of
+    two-step passes its two dphi buffers swap roles, so every call keeps all its pairs."""
+
+    def __init__(self, prs, shape, stream, **kw):
+        self.prs = prs
+        self.params = prs.make_params(shape, **kw)
+        self.handle = prs.prs_create(self.params, stream.cuda_stream)
+
+    def close(self):
+        if self.handle is not None:
+            self.prs.prs_destroy(self.handle)
+            self.handle = None
 
 
-def interval_calls(rest: int, tb: int):
-    """The plain steps of an output interval as two calls (pure, tail) with the same passes as
-    prs_step(rest): `pure` steps that are all passes of the step kernel (with two steps per
-    pass an even number of pairs, which the library splits no further), then the remaining
-    `tail`; events bracket them, so the first bracket times the step kernel alone."""
-    pairs, _ = library_split(rest, tb)
-    pure = 2 * (pairs - pairs % 2) if tb == 2 else rest
+def interval_calls(interval: int, tb: int):
+    """An output interval as (pure, tail) after prs_step_measure(1), which takes the diagnostics of the
+    start state inside a one-step pass: prs_step(pure) is passes of the step kernel only (with two
+    steps per pass an even number of steps), prs_step(tail) the rest (one single step for an even
+    interval).  The run's buffers are library-owned, so the pairs of every call are kept."""
+    rest = interval - 1
+    pure = rest - rest % tb
     return pure, rest - pure
 
 
@@ -300,29 +305,27 @@ def run_gpu(args, world, rank, local):
     shape, desc = WORKLOADS[args.workload]
     sites = int(np.prod(shape))
     stream = torch.cuda.Stream(dev)
-    sim = prs.Sim(shape, precision=prs.PRS_FP32, stream=stream, device=dev, seed=1000 + rank, tblock=args.tblock)
-    sim.init()
+    run = OwnedRun(prs, shape, stream, seed=1000 + rank, tblock=args.tblock)
+    prs.prs_init(run.handle)
     tb = args.tblock if args.tblock > 0 else lib_default_tblock(prs, shape)
-    # one bench step = the diagnostics of the state at the start of an output interval,
-    # fused into its first leapfrog step (prs_step_measure), then the other interval-1
-    # steps (prs_step)
-    rest = args.interval - 1
-    pairs, singles = library_split(rest, tb)
-    step_launches = pairs + singles
-    pure, tail = interval_calls(rest, tb)
+    # one bench step = one output interval: the diagnostics of its start state fused into its
+    # first step (prs_step_measure(1)), then the other steps: prs_step(pure), passes of the step
+    # kernel only (bracketed by events on the run's stream), and prs_step(tail)
+    pure, tail = interval_calls(args.interval, tb)
     pure_launches = pure // tb
+    step_launches = pure_launches + tail
 
     def one_step(events=None):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if events is not None else [None] * 4
         rec = (lambda ev: ev.record(stream)) if events is not None else (lambda ev: None)
         rec(e[0])
-        d = prs.prs_step_measure(sim.handle, 1)
+        d = prs.prs_step_measure(run.handle, 1)
         rec(e[1])
         if pure:
-            prs.prs_step(sim.handle, pure)
+            prs.prs_step(run.handle, pure)
         rec(e[2])
         if tail:
-            prs.prs_step(sim.handle, tail)
+            prs.prs_step(run.handle, tail)
         rec(e[3])
         if events is not None:
             events.append(e)
@@ -344,14 +347,12 @@ def run_gpu(args, world, rank, local):
     barrier(world)
     ms = start.elapsed_time(stop)
     ms_max = allreduce_max(ms, world, dev)
-    # the middle bracket holds only launches of the step kernel (for interval = 20 and two
-    # steps per pass: eight two-step passes), so its mean launch duration is total / launches
+    # the second bracket holds only launches of the step kernel (for interval = 20 and two
+    # steps per pass: nine two-step passes), so its mean launch duration is total / launches
     fused_ms = sum(e[0].elapsed_time(e[1]) for e in events) / len(events)
+    pure_ms = sum(e[1].elapsed_time(e[2]) for e in events) / len(events)
     tail_ms = sum(e[2].elapsed_time(e[3]) for e in events) / len(events)
-    if pure_launches:
-        launch_avg_ms = sum(e[1].elapsed_time(e[2]) for e in events) / (len(events) * pure_launches)
-    else:  # an interval too short for a pure bracket: the plain passes' mean
-        launch_avg_ms = tail_ms / max(step_launches, 1)
+    launch_avg_ms = pure_ms / pure_launches if pure_launches else tail_ms / max(step_launches, 1)
     value = aggregate(sites * args.interval * args.steps, world, ms_max / 1e3)
     # the same timed region as REPEATS equal repeats of consecutive intervals (event pairs
     # per interval, so no extra synchronisation inside the region): their rates and median
@@ -391,7 +392,7 @@ def run_gpu(args, world, rank, local):
         roofline["dram_frac"] = rec["dram_bytes_per_launch"] / (launch_avg_ms / 1e3) / 1e9 / peak
 
     state_gb = sites * 4 * (4 if tb == 2 else 3) / 1e9  # FP32 fields resident on the device
-    e2e = None if args.no_e2e else run_e2e(args, prs, sim, shape, stream, dev, world)
+    e2e = None if args.no_e2e else run_e2e(args, prs, run, shape, stream, dev, world)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "site-updates/s",
@@ -411,7 +412,7 @@ def run_gpu(args, world, rank, local):
         "roofline": roofline, "e2e": e2e, "clocks": clocks,
         "gpu_launches": args.steps * (step_launches + 1),  # one fused step+diagnostics launch per interval
     }
-    sim.close()
+    run.close()
     if rank == 0 and not args.no_2d and args.workload != "2d4096":
         line["fig_2d4096"] = run_2d_figure(prs, stream, dev, args.interval)
     if rank == 0 and not args.no_batch:

@@ -59,20 +59,14 @@ def test_clock_summary(bench):
     assert c.summary()["reasons"] == ["unsampled"]
 
 
-def test_interval_calls_keep_the_library_passes(bench):
-    """The benchmark's two calls per interval run exactly the passes of one prs_step(rest), and
-    the first call holds only launches of the step kernel."""
+def test_interval_calls_split_an_interval(bench):
+    """After the fused step + diagnostics, an interval's other steps are one call of whole passes of
+    the step kernel (the bracket the roofline times) and a remainder shorter than a pass."""
     for tb in (1, 2):
-        for rest in range(0, 64):
-            pure, tail = bench.interval_calls(rest, tb)
-            assert pure + tail == rest and pure >= 0 and tail >= 0
-            p_all, s_all = bench.library_split(rest, tb)
-            p_pure, s_pure = bench.library_split(pure, tb)
-            p_tail, s_tail = bench.library_split(tail, tb)
-            assert (p_pure + p_tail, s_pure + s_tail) == (p_all, s_all), (tb, rest)
-            assert s_pure == 0 if tb == 2 else p_pure == 0
-            assert p_pure % 2 == 0  # dphi is back in the run's own buffer after the first call
-    assert bench.interval_calls(19, 2) == (16, 3) and bench.library_split(19, 2) == (9, 1)
+        for interval in range(1, 64):
+            pure, tail = bench.interval_calls(interval, tb)
+            assert pure + tail == interval - 1 and pure % tb == 0 and 0 <= tail < tb
+    assert bench.interval_calls(20, 2) == (18, 1) and bench.interval_calls(20, 1) == (19, 0)
 
 
 def test_kernel_source_hash_and_traffic_record(bench):
@@ -89,7 +83,7 @@ def test_kernel_source_hash_and_traffic_record(bench):
     assert bench.traffic_record("3d1024", 3 - tb) is None
 
 
-def test_reference_arm_prints_one_json_line():
+def test_reference_arm_prints_one_json_line(bench):
     import oracle
 
     oracle.build()
@@ -100,6 +94,7 @@ def test_reference_arm_prints_one_json_line():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
+    assert d["metric"] == bench.METRIC  # the GPU arm's metric: the driver can form the ratio
     for key in ("metric", "unit", "n_gpus", "ms_per_step", "higher_is_better", "dtype", "config", "cpu_baseline",
                 "e2e"):
         assert key in d
