@@ -651,11 +651,36 @@ def run_precision_figure(prs, stream, dev) -> dict:
     ms = a.elapsed_time(z) / 10
     sim.close()
     torch.cuda.empty_cache()
-    fp64 = {"workload": "3D 512^3 FP64 (generic kernel, FMA allowed)", "ms_per_step": ms,
-            "value": sites / (ms / 1e3), "unit": "site-updates/s",
-            "hbm_bound_value": peak * 1e9 / 32.0, "flops_per_site_update": 18,
-            "achieved_fp64_tflops": 18 * sites / (ms / 1e3) / 1e12,
-            "note": "32 B per site-update in FP64; GB300's FP64 rate is far below its FP32 rate"}
+    # the box's FP64 rate, measured here: a cuBLAS DGEMM through torch (4096^3, best of 5)
+    ga = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    gb = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    torch.matmul(ga, gb)
+    torch.cuda.synchronize(dev)
+    best = float("inf")
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(ga, gb)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del ga, gb
+    torch.cuda.empty_cache()
+    fp64_tflops = 2 * 4096 ** 3 / (best / 1e3) / 1e12
+    # the non-reproducible FP64 step issues 11 double instructions a site-update (5 adds of the
+    # Laplacian's pairs, 2 multiplies, 4 fused multiply-adds), each one issue of the FP64 pipe
+    # that a DGEMM fills with fused multiply-adds (2 flops each)
+    dp_inst = 11
+    alu_bound = fp64_tflops * 1e12 / 2 / dp_inst
+    value = sites / (ms / 1e3)
+    fp64 = {"workload": "3D 512^3 FP64 (generic kernel, folded kick, FMA)", "ms_per_step": ms,
+            "value": value, "unit": "site-updates/s",
+            "bound": "alu", "fp64_peak_tflops_measured": fp64_tflops,
+            "fp64_peak_source": "cuBLAS DGEMM 4096^3 through torch on this GPU, best of 5",
+            "dp_instructions_per_site_update": dp_inst, "alu_bound_value": alu_bound,
+            "frac_of_alu_bound": value / alu_bound, "hbm_bound_value": peak * 1e9 / 32.0,
+            "note": "32 B per site-update in FP64 would allow the HBM-bound value; GB300 issues FP64 at a "
+                    "small fraction of its FP32 rate, so the FP64 pipe bounds the step"}
     # FP32 vs FP64 diagnostics of the same initial field, eta 1 -> 256 (2550 steps), every 10 steps
     # (FP32 with correctly rounded division and square root in the diagnostics: same fields)
     shape2 = (512, 512)

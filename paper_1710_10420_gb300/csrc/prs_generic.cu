@@ -58,6 +58,18 @@ cudaError_t launch_init_random(const Geo& g, int precision, uint64_t seed, void*
     return cudaGetLastError();
 }
 
+// Grid of the row-wise kernels: up to four x blocks per row, y blocks striding over the
+// rows, at most cap blocks in all.
+static dim3 rows_grid(const Geo& g, int cap)
+{
+    const int gx = (g.nx + 255) / 256 < 4 ? (g.nx + 255) / 256 : 4;
+    int64_t gy = cap / gx;
+    const int64_t rows = (int64_t)g.ny * g.nz;
+    if (gy > rows) gy = rows;
+    if (gy < 1) gy = 1;
+    return dim3((unsigned)gx, (unsigned)gy, 1);
+}
+
 // --------------------------------------------------------- generic step
 
 // One site of Eqs. 3-5 in the canonical evaluation order:
@@ -79,35 +91,57 @@ __device__ __forceinline__ void site_update(R c, R xp, R xm, R yp, R ym, R zp, R
     phi_new = A::add(c, A::mul(rc.deta, vn));
 }
 
+// The same step with the step's constants folded on the host (FP64 without PRS_REPRO):
+//   v' = c1 v + g s2 + c (k1 - k2 c^2),  g = c2/dx^2, k1 = c2 cV - 2D g, k2 = c2 cV/phi0^2,
+// which is Eq. 4 rearranged: 11 double operations a site instead of 15.  GB300 issues FP64
+// at a small fraction of its FP32 rate and the generic step is bound by that rate, so the
+// operation count sets its speed.  Every term is odd in phi, so Z2 symmetry stays exact.
+template <int D>
+__device__ __forceinline__ void site_update_folded(double c, double xp, double xm, double yp, double ym, double zp,
+                                                   double zm, double& v, double& phi_new, const KickD& k, double deta)
+{
+    double s2 = xp + xm;
+    s2 = s2 + (yp + ym);
+    if (D == 3) s2 = s2 + (zp + zm);
+    const double u = c * fma(-k.k2, c * c, k.k1);
+    const double vn = fma(k.c1, v, fma(k.g, s2, u));
+    v = vn;
+    phi_new = fma(deta, vn, c);
+}
+
 template <typename R, bool REPRO, int D>
 __global__ void k_step_generic(const R* __restrict__ phi, R* __restrict__ phi_out, const R* dphi, R* dphi_out,
-                               Geo g, StepCoef<R> k, RunConst<R> rc)
+                               Geo g, StepCoef<R> k, RunConst<R> rc, KickD kd)
 {
     const int64_t nx = g.nx, ny = g.ny, nz = g.nz;
     const int64_t plane = nx * ny;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.S; s += (int64_t)gridDim.x * blockDim.x) {
-        int64_t x = s % nx;
-        int64_t r = s / nx;
-        int64_t y = r % ny;
-        int64_t z = r / ny;
-        int64_t row = s - x;
+    // rows of x: y blocks stride over the rows (y, z decoded once per row), x threads over a row
+    for (int64_t r = blockIdx.y; r < ny * nz; r += gridDim.y) {
+        const int64_t y = r % ny, z = r / ny;
+        const int64_t row = r * nx;
+        const int64_t ypo = ((y + 1 == ny ? 0 : y + 1) - y) * nx, ymo = ((y == 0 ? ny - 1 : y - 1) - y) * nx;
+        const int64_t zpo = ((z + 1 == nz ? 0 : z + 1) - z) * plane, zmo = ((z == 0 ? nz - 1 : z - 1) - z) * plane;
+        for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nx; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = row + x;
         R c = phi[s];
         R xp = phi[row + (x + 1 == nx ? 0 : x + 1)];
         R xm = phi[row + (x == 0 ? nx - 1 : x - 1)];
-        int64_t pl = s - y * nx;  // start of this z-plane + x
-        R yp = phi[pl + (y + 1 == ny ? 0 : y + 1) * nx];
-        R ym = phi[pl + (y == 0 ? ny - 1 : y - 1) * nx];
+        R yp = phi[s + ypo];
+        R ym = phi[s + ymo];
         R zp = (R)0, zm = (R)0;
         if (D == 3) {
-            int64_t col = s - z * plane;
-            zp = phi[col + (z + 1 == nz ? 0 : z + 1) * plane];
-            zm = phi[col + (z == 0 ? nz - 1 : z - 1) * plane];
+            zp = phi[s + zpo];
+            zm = phi[s + zmo];
         }
         R v = dphi[s];
         R pn;
-        site_update<R, REPRO, D>(c, xp, xm, yp, ym, zp, zm, v, pn, k, rc);
+        if constexpr (sizeof(R) == 8 && !REPRO)
+            site_update_folded<D>(c, xp, xm, yp, ym, zp, zm, v, pn, kd, rc.deta);
+        else
+            site_update<R, REPRO, D>(c, xp, xm, yp, ym, zp, zm, v, pn, k, rc);
         dphi_out[s] = v;
         phi_out[s] = pn;
+        }
     }
 }
 
@@ -122,15 +156,17 @@ static cudaError_t step_generic_t(const Geo& g, const void* in, void* out, const
                                   double c2, double cV, const double rcd[6], cudaStream_t st)
 {
     const int block = 256;
-    int grid = grid_for(g.S, block);
+    const dim3 grid = rows_grid(g, 152 * 16);
     StepCoef<R> k{(R)c1, (R)c2, (R)cV};
     RunConst<R> rc = make_rc<R>(rcd);
+    const double gq = c2 * rcd[1], h = c2 * cV;  // the folded kick (double): g, k1, k2
+    const KickD kd{c1, gq, h - rcd[3] * gq, h * rcd[2]};
     if (g.dims == 3)
         k_step_generic<R, REPRO, 3><<<grid, block, 0, st>>>((const R*)in, (R*)out, (const R*)dphi, (R*)dphi_out, g, k,
-                                                             rc);
+                                                             rc, kd);
     else
         k_step_generic<R, REPRO, 2><<<grid, block, 0, st>>>((const R*)in, (R*)out, (const R*)dphi, (R*)dphi_out, g, k,
-                                                             rc);
+                                                             rc, kd);
     return cudaGetLastError();
 }
 
@@ -140,18 +176,6 @@ cudaError_t launch_step_generic(const Geo& g, int precision, bool repro, const v
     if (precision == PRS_FP32) return step_generic_t<float, false>(g, in, out, dphi, dphi_out, c1, c2, cV, rcd, st);
     if (repro) return step_generic_t<double, true>(g, in, out, dphi, dphi_out, c1, c2, cV, rcd, st);
     return step_generic_t<double, false>(g, in, out, dphi, dphi_out, c1, c2, cV, rcd, st);
-}
-
-// Grid of the row-wise kernels: up to four x blocks per row, y blocks striding over the
-// rows, at most cap blocks in all.
-static dim3 rows_grid(const Geo& g, int cap)
-{
-    const int gx = (g.nx + 255) / 256 < 4 ? (g.nx + 255) / 256 : 4;
-    int64_t gy = cap / gx;
-    const int64_t rows = (int64_t)g.ny * g.nz;
-    if (gy > rows) gy = rows;
-    if (gy < 1) gy = 1;
-    return dim3((unsigned)gx, (unsigned)gy, 1);
 }
 
 // ------------------------------------------------------------ diagnostics

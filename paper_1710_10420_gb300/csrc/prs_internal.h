@@ -34,6 +34,11 @@ struct KickF {
     float c1, g, k1, k2;
 };
 
+// The FP64 form of KickF (the non-reproducible FP64 step, prs_generic.cu).
+struct KickD {
+    double c1, g, k1, k2;
+};
+
 // Scalars fixed for the whole run, in working precision.
 template <typename R>
 struct RunConst {
