@@ -582,12 +582,19 @@ def run_adjoint_figure(prs, stream, dev, nsteps: int = 1270) -> dict:
             J, dA = prs.prs_adjoint(sim.handle, nsteps, prs.PRS_OBS_SMOOTH_AREA, 0.1, K, g, None)
             torch.cuda.synchronize(dev)
             times.append(time.perf_counter() - t0)
+        phases = prs.prs_adjoint_timing(sim.handle)  # of the second call
         sim.close()
         del g
         torch.cuda.empty_cache()
+        fwd_step_ms = ms_fwd / nsteps
         res[key] = {"adjoint_s": times[1], "adjoint_over_forward": times[1] / (ms_fwd / 1e3),
-                    "first_call_s": times[0], "J": J, "dJ_dalpha": dA}
-    res["note"] = ("adjoint_s covers the forward pass (with checkpoints or stored states), any segment "
+                    "first_call_s": times[0], "J": J, "dJ_dalpha": dA, "phases_ms": phases,
+                    "reverse_step_ms": phases["reverse_ms"] / nsteps,
+                    "reverse_step_over_forward_step": phases["reverse_ms"] / nsteps / fwd_step_ms,
+                    "recompute_step_over_forward_step": phases["recompute_ms"] / nsteps / fwd_step_ms}
+    res["forward_step_ms"] = ms_fwd / nsteps
+    res["note"] = ("reverse_step_over_forward_step: one reverse (adjoint) step against one forward step, the "
+                   "per-step cost; adjoint_s covers the forward pass (with checkpoints or stored states), any segment "
                    "recomputation and the reverse sweep, with the run's working memory already allocated "
                    f"(first_call_s includes allocating it); keep_all stores all {nsteps + 1} states in HBM")
     return res

@@ -209,6 +209,25 @@ int prs_set_state_async(prs_sim* sim, const void* h_phi, const void* h_dphi, int
  * event).  A source that already is the run's current buffer is left in place. */
 int prs_set_state_device(prs_sim* sim, const void* d_phi, const void* d_dphi, int64_t n);
 
+/* Change the conformal time step from the current step n on (the physical equations,
+ * alpha = beta = 2, stiffen as a^beta grows: a fixed deta that is stable early fails the
+ * stability limit later).  Conformal time continues from the current eta_n:
+ * eta_m = eta_n + (m - n) deta for the following steps (params.eta0 is re-based to
+ * eta_n - n deta; diagnostics report eta_m).  The kick of the first step with the new
+ * deta starts from the stored dphi^{n-1/2} of the old step, as the scheme of Eqs. 4-5
+ * does at every step.  PRS_EINVAL if deta <= 0 or if a step of deta at eta_n is unstable
+ * or has delta >= 1.  Takes effect for the next queued step (no synchronisation). */
+int prs_set_deta(prs_sim* sim, double deta);
+
+/* The largest stable time step at conformal time eta for these parameters:
+ * 2 / sqrt(4D/dx^2 + 2 cV(eta) phi0^2), cV(eta) = 4 V0 a(eta)^beta / phi0^2, a = eta^era_m
+ * (the leapfrog's limit for the stiffest lattice mode, with the force's slope at its largest
+ * for |phi| <= phi0, 2 cV).  A field that overshoots the vacua is stiffer (slope
+ * cV (3 phi^2/phi0^2 - 1)): the physical equations (beta = 2), whose walls thin below the
+ * lattice spacing, overshoot by tens of per cent, so a schedule should keep a margin (half
+ * of this value carries a 2D run with W0 = 8 to eta = 100). */
+int prs_stable_deta(const prs_params* params, double eta, double* deta_max);
+
 /* Device pointers of the current fields and the step index (any output may be
  * NULL).  The pointers stay valid until the next prs_step or prs_destroy (a run with
  * library-owned buffers may hold dphi in either of its two dphi buffers). */
@@ -298,6 +317,13 @@ int prs_observable(prs_sim* sim, int observable, double eps_smooth, double* J);
  * On return the run holds the state at step n+nsteps.  Synchronises. */
 int prs_adjoint(prs_sim* sim, int64_t nsteps, int observable, double eps_smooth, int64_t ckpt_every, double* J,
                 double* dJ_dalpha, void* d_dJ_dphi_init, void* d_dJ_dv_init);
+
+/* Where the time of the last successful prs_adjoint call on this run went, in
+ * milliseconds, from CUDA events recorded on the run's stream: ms[0] the forward pass
+ * (with its checkpoints or stored states, and J), ms[1] the recomputation of the
+ * segments' states, ms[2] the reverse sweep (the reverse steps).  PRS_ESTATE before any
+ * such call. */
+int prs_adjoint_timing(prs_sim* sim, double ms[3]);
 
 /* Step-n coefficients as the library computes them on the host in FP64:
  * out[0] = c1 = (1-delta_n)/(1+delta_n), out[1] = c2 = deta/(1+delta_n) (Eq. 4, 6),

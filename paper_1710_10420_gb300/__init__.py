@@ -129,6 +129,9 @@ _SIGS = {
     "prs_adjoint": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _DP, _DP, _VP,
                                    _VP]),
     "prs_measure_noalloc": (ctypes.c_int, [_P, _VP, _VP, _VP, ctypes.POINTER(prs_diag)]),
+    "prs_adjoint_timing": (ctypes.c_int, [_VP, _DP]),
+    "prs_set_deta": (ctypes.c_int, [_VP, ctypes.c_double]),
+    "prs_stable_deta": (ctypes.c_int, [_P, ctypes.c_double, _DP]),
     "prs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "prs_last_error": (ctypes.c_char_p, []),
 }
@@ -341,6 +344,23 @@ def prs_default_tblock(params: prs_params) -> int:
     if rc < 0:
         _check(rc, "prs_default_tblock")
     return rc
+
+
+def prs_set_deta(sim, deta: float) -> None:
+    _check(load().prs_set_deta(sim, deta), "prs_set_deta")
+
+
+def prs_stable_deta(params: prs_params, eta: float) -> float:
+    out = ctypes.c_double()
+    _check(load().prs_stable_deta(ctypes.byref(params), eta, ctypes.byref(out)), "prs_stable_deta")
+    return out.value
+
+
+def prs_adjoint_timing(sim) -> dict:
+    """Phase times of the last prs_adjoint call (ms): forward, recompute, reverse."""
+    out = (ctypes.c_double * 3)()
+    _check(load().prs_adjoint_timing(sim, out), "prs_adjoint_timing")
+    return dict(forward_ms=out[0], recompute_ms=out[1], reverse_ms=out[2])
 
 
 def prs_strerror(status: int) -> str:

@@ -726,6 +726,16 @@ static int prs_adjoint_impl(prs_sim* s, int64_t nsteps, int observable, double e
     } while (0)
 
     DiagScratch scr = s->scr;
+    // phase boundaries for prs_adjoint_timing: start, end of the forward (with J), then the
+    // start of each segment's recomputation and of its reverse sweep, then the end
+    const size_t nev = 3 + 2 * (size_t)nseg;
+    while (s->adj_ev.size() < nev) {
+        cudaEvent_t e;
+        PRS_TRY(cudaEventCreate(&e));
+        s->adj_ev.push_back(e);
+    }
+    s->adj_timed = false;
+    PRS_TRY(cudaEventRecord(s->adj_ev[0], st));
     // Fill the states k_from+1 .. k_to (slot(k): phi of state k, dphi at + fs) from state
     // k_from, step n_first + k_from onwards: in pairs through the two-step pass, which
     // also stores the state between its two steps (FP32 3D boxes it takes, without
@@ -780,12 +790,15 @@ static int prs_adjoint_impl(prs_sim* s, int64_t nsteps, int observable, double e
     // J and dJ/dphi at the end; lt = lv + deta lphi = deta dJ/dphi there (lv = 0)
     PRS_TRY(launch_observable(s, s->phi[s->cur], lphi, lt[0], observable, eps_smooth, scr));
     PRS_TRY(cudaMemcpyAsync(s->h_status, s->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    PRS_TRY(cudaEventRecord(s->adj_ev[1], st));
     int cur = 0;
     for (int64_t i = nseg - 1; i >= 0; --i) {
         const int64_t a = n0 + i * K;
         const int64_t len = (i + 1) * K <= nsteps ? K : nsteps - i * K;
+        PRS_TRY(cudaEventRecord(s->adj_ev[2 + 2 * (size_t)(nseg - 1 - i)], st));
         if (!keep_all)  // recompute states a+1 .. a+len-1
             PRS_TRY(fill([&](int64_t k) { return state(k, i); }, a, 0, len - 1));
+        PRS_TRY(cudaEventRecord(s->adj_ev[3 + 2 * (size_t)(nseg - 1 - i)], st));
         for (int64_t k = len - 1; k >= 0; --k) {
             double c[5];
             step_coefficients(s->p, a + k, c);
@@ -798,6 +811,7 @@ static int prs_adjoint_impl(prs_sim* s, int64_t nsteps, int observable, double e
             cur = 1 - cur;
         }
     }
+    PRS_TRY(cudaEventRecord(s->adj_ev[nev - 1], st));
     if (d_dJ_dphi_init) PRS_TRY(cudaMemcpyAsync(d_dJ_dphi_init, lphi, fbytes, cudaMemcpyDeviceToDevice, st));
     if (d_dJ_dv_init) {
         if (nsteps > 0)
@@ -813,6 +827,20 @@ static int prs_adjoint_impl(prs_sim* s, int64_t nsteps, int observable, double e
     PRS_TRY(cudaMemcpyAsync(&s->h_status->error, &s->d_status->error, sizeof(unsigned int), cudaMemcpyDeviceToHost,
                             st));
     PRS_TRY(cudaStreamSynchronize(st));
+    {
+        float f = 0.0f;
+        double t[3] = {0.0, 0.0, 0.0};
+        PRS_TRY(cudaEventElapsedTime(&f, s->adj_ev[0], s->adj_ev[1]));
+        t[0] = f;
+        for (int64_t r = 0; r < nseg; ++r) {
+            PRS_TRY(cudaEventElapsedTime(&f, s->adj_ev[2 + 2 * r], s->adj_ev[3 + 2 * r]));
+            t[1] += f;
+            PRS_TRY(cudaEventElapsedTime(&f, s->adj_ev[3 + 2 * r], s->adj_ev[r + 1 < nseg ? 4 + 2 * r : nev - 1]));
+            t[2] += f;
+        }
+        for (int q = 0; q < 3; ++q) s->adj_ms[q] = t[q];
+        s->adj_timed = true;
+    }
 #undef PRS_TRY
     int rc = check_device_error(s);
     if (rc) return rc;
@@ -820,6 +848,14 @@ static int prs_adjoint_impl(prs_sim* s, int64_t nsteps, int observable, double e
     for (int64_t k = 0; k < nsteps; ++k) da += hacc[(size_t)k].sum_w;  // fixed order: step index
     if (J) *J = Jv;
     if (dJ_dalpha) *dJ_dalpha = da;
+    return PRS_OK;
+}
+
+extern "C" int prs_adjoint_timing(prs_sim* s, double ms[3])
+{
+    if (!s || !ms) return PRS_EINVAL;
+    if (!s->adj_timed) return PRS_ESTATE;
+    for (int q = 0; q < 3; ++q) ms[q] = s->adj_ms[q];
     return PRS_OK;
 }
 

@@ -117,6 +117,20 @@ extern "C" int prs_coefficients(const prs_params* params, int64_t n, double out[
     return PRS_OK;
 }
 
+// Largest stable time step at conformal time eta: deta^2 (4D/dx^2 + 2 cV(eta) phi0^2) < 4.
+extern "C" int prs_stable_deta(const prs_params* params, double eta, double* deta_max)
+{
+    if (!params || !deta_max || !(eta > 0) || !isfinite(eta)) return PRS_EINVAL;
+    prs_params q = *params;
+    q.eta0 = eta;  // step 0 of q is at eta
+    double c[5];
+    step_coefficients(q, 0, c);
+    const double lam = 4.0 * q.dims / (q.dx * q.dx) + 2.0 * c[2] * q.phi0 * q.phi0;
+    if (!(lam > 0) || !isfinite(lam)) return PRS_EINVAL;
+    *deta_max = 2.0 / sqrt(lam);
+    return PRS_OK;
+}
+
 extern "C" int prs_default_tblock(const prs_params* params)
 {
     Geo g;
@@ -241,6 +255,7 @@ extern "C" int prs_destroy(prs_sim* s)
     cudaFree(s->scr.partials);
     cudaFree(s->dphi_alt);
     cudaFree(s->adj_ws);
+    for (cudaEvent_t e : s->adj_ev) cudaEventDestroy(e);
     cudaFreeHost(s->h_status);
     delete s;
     return PRS_OK;
@@ -363,6 +378,25 @@ extern "C" int prs_device_state(prs_sim* s, void** d_phi, void** d_dphi, int64_t
     if (n) *n = s->n;
     return PRS_OK;
 }
+
+// From the next step on, steps of size deta: eta continues from the current time,
+// eta_m = eta_n + (m - n) deta for the current step n (eta0 is re-based to eta_n - n deta).
+static int set_deta(prs_sim* s, double deta)
+{
+    if (!s || !(deta > 0) || !isfinite(deta)) return PRS_EINVAL;
+    prs_params q = s->p;
+    const double eta_n = s->p.eta0 + (double)s->n * s->p.deta;
+    q.eta0 = eta_n - (double)s->n * deta;
+    q.deta = deta;
+    double c[5];
+    step_coefficients(q, s->n, c);
+    if (!cfl_ok(q, s->n) || !(c[3] < 1.0)) return PRS_EINVAL;
+    s->p = q;
+    s->rc[0] = deta;
+    return PRS_OK;
+}
+
+extern "C" int prs_set_deta(prs_sim* s, double deta) { return set_deta(s, deta); }
 
 // ------------------------------------------------------ launcher setup
 

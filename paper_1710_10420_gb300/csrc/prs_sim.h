@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "prs.h"
 #include "prs_internal.h"
 
@@ -26,6 +28,9 @@ struct prs_sim {
     void* dphi_alt;           // second dphi buffer for passes that read dphi across sites (library-owned)
     void* adj_ws;             // prs_adjoint working memory, kept for the next call
     size_t adj_ws_bytes;
+    std::vector<cudaEvent_t> adj_ev; // prs_adjoint phase boundaries (created on demand)
+    double adj_ms[3];         // last prs_adjoint: forward, recomputation, reverse sweep (ms)
+    bool adj_timed;
     void* guard_base[3];      // PRS_DEBUG: allocations of phi[0], phi[1], dphi with guard bands
     prs::DebugCheck* d_dbg;   // PRS_DEBUG: results of the scan kernel
 };

@@ -155,3 +155,27 @@ def test_autograd_function():
     assert _rel(phi0.grad.cpu().numpy(), 2.0 * ref["dJ_dphi"]) <= 1e-10
     assert _rel(v0.grad.cpu().numpy(), 2.0 * ref["dJ_dv"]) <= 1e-10
     assert float(alpha.grad) == pytest.approx(2.0 * ref["dJ_dalpha"], rel=1e-10)
+
+
+def test_adjoint_timing_reports_the_phases():
+    """prs_adjoint_timing: the forward, recomputation and reverse-sweep times of the last call, from
+    events on the run's stream; no recomputation when every state is kept."""
+    import time
+
+    shape = (128, 32, 16)
+    sim = prs.Sim(shape, precision=prs.PRS_FP32, seed=3)
+    sim.init()
+    with pytest.raises(prs.PRSError) as e:
+        prs.prs_adjoint_timing(sim.handle)
+    assert e.value.status == prs.PRS_ESTATE
+    t0 = time.perf_counter()
+    prs.prs_adjoint(sim.handle, 40, prs.PRS_OBS_GRAD_ENERGY, 0.1, 8, None, None)
+    wall = (time.perf_counter() - t0) * 1e3
+    t = prs.prs_adjoint_timing(sim.handle)
+    assert t["forward_ms"] > 0 and t["recompute_ms"] > 0 and t["reverse_ms"] > 0
+    assert t["forward_ms"] + t["recompute_ms"] + t["reverse_ms"] <= wall
+    sim.init()
+    prs.prs_adjoint(sim.handle, 40, prs.PRS_OBS_GRAD_ENERGY, 0.1, 0, None, None)
+    t = prs.prs_adjoint_timing(sim.handle)
+    assert t["recompute_ms"] < 0.05 * t["reverse_ms"]  # events only: nothing is recomputed
+    sim.close()

@@ -55,6 +55,64 @@ def test_physical_alpha_beta_2(shape):
     assert np.max(np.abs(phi - ophi)) / np.max(np.abs(ophi)) <= 1e-5
 
 
+def test_physical_equations_with_a_smaller_late_time_step():
+    """alpha = beta = 2 stiffens as a^beta = eta^2 grows: with deta = 0.1 the field overshoots the
+    vacua and blows up near eta = 20 (2D, W0 = 8).  prs_set_deta shrinks the step from the current
+    one on; FP64 repro runs stay bit-identical to the oracle run in two segments, the second with
+    eta0 re-based so that eta continues (eta_m = eta_n + (m - n) deta)."""
+    shape = (48, 40)
+    kw = dict(alpha=2.0, beta=2.0, era_m=1.0, W0=8.0)
+    sim = prs.Sim(shape, precision=prs.PRS_FP64, flags=prs.PRS_REPRO, seed=9, **kw)
+    sim.init()
+    sim.step(150)  # eta 1 -> 16
+    with pytest.raises(prs.PRSError):
+        sim.step(200)  # would reach eta = 36 with deta = 0.1: unstable, refused before any work
+    prs.prs_set_deta(sim.handle, 0.05)
+    sim.step(300)  # eta 16 -> 31
+    phi, v, n = sim.get_state()
+    d = sim.measure()
+    sim.close()
+    p1 = oracle.Params(shape, **kw)
+    ophi, ov = oracle.step(p1, *oracle.init_random(p1, 9), 150)
+    eta_n = 1.0 + 150 * 0.1
+    p2 = oracle.Params(shape, deta=0.05, eta0=eta_n - 150 * 0.05, **kw)
+    ophi, ov = oracle.step(p2, ophi, ov, 300, n0=150)
+    assert np.all(np.isfinite(ophi)) and np.max(np.abs(ophi)) < 1.5
+    assert n == 450 and np.array_equal(phi, ophi) and np.array_equal(v, ov)
+    assert d["eta"] == pytest.approx(eta_n + 300 * 0.05, rel=1e-15)
+    od = oracle.measure(p2, ophi, ov)
+    assert (d["n_links"], d["n_wall"]) == (od.n_links, od.n_wall)
+
+
+def test_late_time_schedule_reaches_eta_100():
+    """A schedule of shrinking steps (each chunk takes half the largest stable step at the chunk's
+    end: prs_stable_deta assumes |phi| <= phi0, and the field overshoots the vacua by up to ~40%)
+    carries the physical equations to eta = 100 in FP32 on the staged kernels; the fixed step is
+    refused before eta = 40."""
+    shape = (256, 256)
+    kw = dict(alpha=2.0, beta=2.0, era_m=1.0, W0=8.0)
+    params = prs.make_params(shape, **kw)
+    sim = prs.Sim(shape, precision=prs.PRS_FP32, seed=2, **kw)
+    sim.init()
+    deta, eta, chunk = 0.1, 1.0, 20
+    while eta < 100.0:
+        limit = prs.prs_stable_deta(params, eta + chunk * deta)
+        if deta > 0.5 * limit:
+            deta = 0.5 * limit
+            prs.prs_set_deta(sim.handle, deta)
+        sim.step(chunk)
+        eta = prs.prs_measure_ex(sim.handle).eta
+    phi, v, n = sim.get_state()
+    sim.close()
+    assert eta >= 100.0 and np.all(np.isfinite(phi)) and np.all(np.isfinite(v)) and np.max(np.abs(phi)) < 2.0
+    fixed = prs.Sim(shape, precision=prs.PRS_FP32, seed=2, **kw)
+    fixed.init()
+    with pytest.raises(prs.PRSError):
+        for _ in range(20):
+            fixed.step(20)  # eta 1 -> 41 in steps of 0.1
+    fixed.close()
+
+
 SHAPE, STEPS, EVERY, SEEDS = (512, 512), 630, 10, 8
 
 
