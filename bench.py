@@ -240,8 +240,9 @@ def peaks():
 
 # the sources that define the FP32 step kernels (device code and the structs they take),
 # by steps per pass
-STEP_KERNEL_SOURCES = {1: ("prs_fast.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_reduce.cuh"),
-                       2: ("prs_tblock.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h")}
+STEP_KERNEL_SOURCES = {1: ("prs_fast.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_reduce.cuh",
+                           "prs_f32x2.cuh"),
+                       2: ("prs_t2tma.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_f32x2.cuh")}
 
 
 def kernel_sources_sha(names=STEP_KERNEL_SOURCES[2]) -> str:
@@ -376,7 +377,7 @@ def run_gpu(args, world, rank, local):
     rec = traffic_record(args.workload, tb)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (rec["dram_bytes_per_launch"] if rec else None),
-                "kernel": ("k_step3d_t2, two leapfrog steps per pass" if tb == 2 else
+                "kernel": ("k_step3d_t2tma, two leapfrog steps per pass" if tb == 2 else
                            "k_step3d_f32, one leapfrog step per pass") if len(shape) == 3 else
                           f"2D step kernel, {tb} leapfrog step(s) per pass",
                 "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_site_update": alg_bytes / (sites * tb),
