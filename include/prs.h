@@ -264,9 +264,10 @@ int prs_destroy(prs_sim* sim);
  * of 128 dividing 4096 (3D: at most 1024) and 4096/x dividing the y side. */
 
 /* Create an ensemble of nruns runs (each validated as by prs_create), allocate all
- * fields, pick tile lengths and the L2 grouping by timing short trials on them
- * (the autotuner), then set every run to its seeded random initial condition
- * (step 0).  stream may be NULL (the ensemble then creates its own stream). */
+ * fields, pick a tile length for each geometry class of runs (4 to 32 planes or bands)
+ * and the L2 grouping by timing short trials on them (the autotuner), then set every
+ * run to its seeded random initial condition (step 0).  stream may be NULL (the
+ * ensemble then creates its own stream). */
 int prs_batch_create(const prs_params* runs, int nruns, void* stream, prs_batch** out);
 
 /* Advance run r by nsteps_per_run[r] (>= 0) steps in one persistent launch.  With

@@ -111,7 +111,9 @@ def test_diagnostics_at_step_zero_random_fields():
 
 
 def test_batch_is_deterministic_and_matches_single_runs():
-    """Two fresh ensembles give identical bits; each run agrees with prs_step + prs_measure."""
+    """Two fresh ensembles give identical fields and counts (the diagnostic sums group per-tile
+    partials in FP64, so tile lengths picked by the timing-based autotuner may regroup them:
+    1e-12); each run agrees with prs_step + prs_measure."""
     runs = RUNS[:5]
     ns = [12, 9, 10, 8, 13]
     outs, states = [], []
@@ -125,7 +127,8 @@ def test_batch_is_deterministic_and_matches_single_runs():
             st.append(phi)
         states.append(st)
         prs.prs_batch_destroy(b)
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0][..., [0, 3]], outs[1][..., [0, 3]])  # steps and link counts
+    assert np.allclose(outs[0], outs[1], rtol=1e-12, atol=0)
     for a, c in zip(states[0], states[1]):
         assert np.array_equal(a, c)
     for r, (shape, era, seed, _) in enumerate(runs):
@@ -138,11 +141,14 @@ def test_batch_is_deterministic_and_matches_single_runs():
 
 
 def test_autotuner_reports_a_choice():
-    b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd, _ in RUNS[:3]])
+    """One tile length per geometry class, from the candidates 4 .. 32."""
+    runs = RUNS[:3] + RUNS[:3]
+    b = prs.prs_batch_create([_params(s, e, sd + 100 * (i >= 3)) for i, (s, e, sd, _) in enumerate(runs)])
     try:
-        for r in range(3):
-            t, g = prs.prs_batch_tuning(b, r)
-            assert t in (8, 16, 32, 64) and g > 0
+        t = [prs.prs_batch_tuning(b, r)[0] for r in range(len(runs))]
+        assert all(x in (4, 8, 16, 32) for x in t) and prs.prs_batch_tuning(b, 0)[1] > 0
+        for r in range(3):  # runs of one box share their class's choice
+            assert t[r] == t[r + 3] or runs[r][0] != runs[r + 3][0]
     finally:
         prs.prs_batch_destroy(b)
 
