@@ -79,6 +79,25 @@ def test_fp32_adjoint_matches_oracle(shape, obs, K):
     assert dA == pytest.approx(ref["dJ_dalpha"], rel=1e-5)
 
 
+@pytest.mark.parametrize("K", [8, 5, 0])
+def test_fp32_adjoint_on_a_tensor_copy_box(K):
+    """512-wide 3D rows: the forward and the stored or recomputed states go through the two-step
+    pass with tensor copies, its variant that also stores the state between the two steps."""
+    shape, nsteps = (512, 16, 8), 22
+    p = oracle.Params(shape, W0=6.0, eta0=2.0)
+    phi0 = (0.8 * inp.random_field(shape, seed=31)).astype(np.float32)
+    v0 = (0.05 * inp.random_field(shape, seed=32)).astype(np.float32)
+    ref = oracle.adjoint(p, phi0.astype(np.float64), v0.astype(np.float64), nsteps, 1, eps=0.1)
+    J, dA, gphi, gv, end_phi, n = _gpu_adjoint(shape, prs.PRS_FP32, phi0, v0, nsteps, 1, K, eps=0.1, W0=6.0,
+                                                eta0=2.0)
+    assert n == nsteps
+    assert J == pytest.approx(ref["J"], rel=1e-5)
+    assert _rel(gphi, ref["dJ_dphi"]) <= 1e-5 and _rel(gv, ref["dJ_dv"]) <= 1e-5
+    assert dA == pytest.approx(ref["dJ_dalpha"], rel=1e-5)
+    ophi, _ = oracle.step(p, phi0.astype(np.float64), v0.astype(np.float64), nsteps)
+    assert _rel(end_phi, ophi) <= 1e-5
+
+
 @pytest.mark.parametrize("K", [8, 0])
 @pytest.mark.parametrize("shape", [(128, 32, 8), (256, 16, 12), (256, 64)])
 def test_fp32_adjoint_configured_smoothing(shape, K):

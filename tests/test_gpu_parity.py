@@ -144,6 +144,20 @@ def test_fp32_temporal_blocks(shape, tblock, nsteps):
     assert _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
 
 
+@pytest.mark.parametrize("nsteps", [2, 7, 12])
+@pytest.mark.parametrize("shape", [(512, 16, 12), (768, 24, 9), (1280, 16, 5), (512, 32, 3), (1024, 40, 17)])
+def test_tensor_copy_two_step_pass(shape, nsteps):
+    """The two-step pass with TMA tensor copies (x sides multiples of 256, at least 512; y sides
+    multiples of 8, at least 16): x tiles at both periodic ends and inside, both y-wrapping tiles
+    (ny = 16: every tile wraps), the minimal z side, uneven z chunks; fields to 1e-5 of the oracle."""
+    p = oracle.Params(shape)
+    ophi, ov = oracle.init_random(p, 21)
+    ov = 0.1 * inp.random_field(shape, 22)
+    phi, v = _run(shape, prs.PRS_FP32, nsteps, ophi.astype(np.float32), ov.astype(np.float32), seed=21, tblock=2)
+    ophi, ov = oracle.step(p, ophi, ov, nsteps)
+    assert _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
+
+
 @pytest.mark.parametrize("shape", [(256, 64, 48), (1024, 32, 24)])
 def test_two_step_passes_match_single_steps(shape):
     """Two-step passes and one-step passes agree to FP32 rounding over many passes (3D: whole rows
