@@ -341,10 +341,13 @@ bool encode(EncodeTiled f, CUtensorMap* m, const float* base, const Geo& g, unsi
 }  // namespace
 
 // The tensor-copy pass applies to FP32 3D boxes tiled by 256 x 8 (x side a multiple of
-// 256 and at least 512, y side a multiple of 8 and at least 16, z side at least 3).
+// 256, y side a multiple of 8 and at least 16, z side at least 3).  With a 256-wide row the
+// tile is the whole row: its halo boxes hold the row's own wrapped end columns, and the halo
+// lanes compute two columns the row's float4 also compute (the same operations, so the same
+// bits).
 bool t2tma_ok(const Geo& g)
 {
-    return g.dims == 3 && g.nx % kXW == 0 && g.nx >= 2 * kXW && g.ny % kTY == 0 && g.ny >= 2 * kTY && g.nz >= 3;
+    return g.dims == 3 && g.nx % kXW == 0 && g.ny % kTY == 0 && g.ny >= 2 * kTY && g.nz >= 3;
 }
 
 cudaError_t launch_step_t2_tma(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
