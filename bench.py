@@ -185,6 +185,28 @@ def oracle_sample(interval: int, shape=(64, 64, 64)):
     return p.sites * interval, dt
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(interval: int) -> dict:
     """The oracle as it stands, single-threaded on this host: 128^3, two output intervals."""
     shape = (128, 128, 128)
@@ -195,7 +217,8 @@ def cpu_baseline(interval: int) -> dict:
         secs += s
     return {"value": units / secs, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 oracle, 3D 128^3, 2 x ({interval} leapfrog steps + diagnostics), "
-                      f"{secs:.1f} s on {os.cpu_count()} host cores (1 used)"}
+                      f"{secs:.1f} s on {os.cpu_count()} host cores (1 used)",
+            "host_cores": os.cpu_count(), "cpu_model": cpu_model()}
 
 
 def run_reference(args, world, rank):
@@ -219,7 +242,8 @@ def run_reference(args, world, rank):
                    "interval": args.interval,
                    "reference": "the FP64 CPU oracle (no reference implementation exists), single-threaded"},
         "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"3D 64^3, {args.interval} leapfrog steps + diagnostics per step"},
+                         "sample": f"3D 64^3, {args.interval} leapfrog steps + diagnostics per step",
+                         "host_cores": os.cpu_count(), "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
