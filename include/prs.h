@@ -109,8 +109,11 @@ typedef struct {
                           and FP32 2D boxes of at least 2^24 sites, else 1; see
                           prs_default_tblock); 2 = two-step passes for FP32 boxes with
                           an x side that is a multiple of 128 (3D; z side >= 3) or a
-                          multiple of 128 up to 4096 (2D), else 1; at most 8 (values
-                          above 2 act as 2)                                         */
+                          multiple of 128 up to 4096 (2D), else 1; 3 = three-step
+                          passes for FP32 3D boxes with an x side that is a multiple
+                          of 128, a y side that is a multiple of 8 (at least 16) and
+                          a z side >= 3, else as 2; at most 8 (values above the
+                          box's limit act as that limit)                            */
 } prs_params;
 
 /* One output record of the wall diagnostics (Eq. 7, Eq. 8). */
@@ -154,19 +157,20 @@ int prs_init(prs_sim* sim, const void* h_phi, const void* h_dphi);
  * without waiting (the call never allocates, so it may be captured into a CUDA graph).
  * Step n uses delta_n, eta_n = eta0 + n deta.  Every step of the call must satisfy the
  * stability limit (checked at both ends, where the force prefactor a^beta is largest),
- * else PRS_EINVAL.  Passes of two steps (see prs_params.tblock) read dphi across sites
- * and write it out of place, into a second dphi buffer that prs_init, prs_set_state or
- * prs_set_state_device allocate when the run takes two-step passes (owned by the run,
- * freed by prs_destroy; if that allocation fails, the steps run one per pass).
- * Where dphi ends:
+ * else PRS_EINVAL.  Passes of two or three steps (see prs_params.tblock) read dphi
+ * across sites and write it out of place, into a second dphi buffer that prs_init,
+ * prs_set_state or prs_set_state_device allocate when the run takes multi-step passes
+ * (owned by the run, freed by prs_destroy; if that allocation fails, the steps run one
+ * per pass).  A call of nsteps runs nsteps / T passes of T = tblock steps, then (T = 3)
+ * one pair if two steps remain, then single steps.  Where dphi ends:
  *   - library-owned buffers (no prs_bind, no PRS_DEBUG): after an odd number of
- *     two-step passes the two dphi buffers swap roles; every step count keeps all its
- *     pairs.  prs_device_state returns the current buffer.
+ *     multi-step passes the two dphi buffers swap roles; every step count keeps all its
+ *     passes.  prs_device_state returns the current buffer.
  *   - bound buffers (prs_bind) or PRS_DEBUG: dphi ends in the run's own buffer after
- *     every call.  An odd step count keeps all its pairs (the last single step brings
- *     dphi home); an even count whose pairs are odd in number (2, 6, 10, ...) runs one
- *     pair as two single steps, so a caller stepping by a multiple of 4 (or an odd count)
- *     gets only two-step passes. */
+ *     every call.  After an odd number of multi-step passes the first single step brings
+ *     dphi home; with no single step to do it, the last pair runs as two single steps
+ *     (T = 2: counts 2, 6, 10, ...; T = 3: counts 2, 8, 14, ...) or the last triple as a
+ *     pair and a single step (T = 3: counts 3, 9, 15, ...). */
 int prs_step(prs_sim* sim, int64_t nsteps);
 
 /* Wall diagnostics of the current state (Eq. 7, Eq. 8), reduced on the device in

@@ -444,45 +444,72 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
     if (!cfl_ok_over(s->p, s->n, nsteps)) return PRS_EINVAL;
     const bool repro = (s->p.flags & PRS_REPRO) != 0;
     const int tb = run_tblock(s);
-    // Two-step passes read dphi across sites, so they write it to a second buffer.
-    // After an odd number of them dphi sits in that buffer.  A run whose buffers the
-    // library owns (no PRS_DEBUG guard bands) then just swaps the roles of its two dphi
-    // buffers.  A run with bound buffers keeps dphi in the bound buffer at the end of
-    // every call: the single step after an odd number of pairs reads dphi in the second
-    // buffer and writes the bound one, so an odd step count keeps every pair; with an
-    // even count and an odd number of pairs, one pair runs as two single steps instead.
-    // Single steps otherwise update dphi in place.
+    // Multi-step passes (two or three steps) read dphi across sites, so they write it to a
+    // second buffer; a call runs `big` passes of tb steps, then (tb = 3) at most one pair, then
+    // single steps.  After an odd number of multi-step passes dphi sits in the second buffer.  A
+    // run whose buffers the library owns (no PRS_DEBUG guard bands) then just swaps the roles of
+    // its two dphi buffers.  A run with bound buffers keeps dphi in the bound buffer at the end of
+    // every call: the first single step after an odd number of multi-step passes reads dphi in
+    // the second buffer and writes the bound one; with no single step to do it, the last pair
+    // runs as two single steps (tb = 2, or the pair of tb = 3) or the last triple as a pair and a
+    // single step.  Single steps otherwise update dphi in place.
     const bool swap_ok = s->owned && (s->p.flags & PRS_DEBUG) == 0;
-    int64_t pairs = tb == 2 ? nsteps / 2 : 0;
-    if ((pairs & 1) && nsteps == 2 * pairs && !swap_ok) --pairs;
-    if (pairs > 0 && !s->dphi_alt) pairs = 0;  // no second buffer (no room at prs_init): single steps
-    const int64_t singles = nsteps - 2 * pairs;
-    const bool swap_home = (pairs & 1) && singles == 0;  // only when swap_ok
+    int64_t big = tb >= 2 ? nsteps / tb : 0;
+    int64_t pairs = (tb == 3 && nsteps - big * tb == 2) ? 1 : 0;
+    int64_t singles = nsteps - big * tb - 2 * pairs;
+    if (!s->dphi_alt) big = pairs = 0, singles = nsteps;  // no second buffer (no room at prs_init)
+    if (((big + pairs) & 1) && singles == 0 && !swap_ok) {
+        if (pairs) pairs = 0, singles = 2;
+        else if (tb == 3) --big, pairs = 1, singles = 1;
+        else --big, singles = 2;
+    }
     unsigned int* err = &s->d_status->error;
     const RunConst<float> rcf{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
                               (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
     void* vbuf[2] = {s->dphi, s->dphi_alt};
-    for (int64_t k = 0; k < pairs; ++k) {
-        double a[5], b[5];
-        const int64_t n = s->n + 2 * k;
+    int vi = 0;  // vbuf[vi] holds dphi
+    int64_t n = s->n;
+    for (int64_t k = 0; k < big + pairs; ++k) {
+        const int t = k < big ? tb : 2;
+        double a[5], b[5], c[5];
         step_coefficients(s->p, n, a);
         step_coefficients(s->p, n + 1, b);
-        cudaError_t e = launch_step_t2(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
-                                       (const float*)vbuf[k & 1], (float*)vbuf[1 - (k & 1)],
-                                       kick_f32(a, s->rc), kick_f32(b, s->rc), rcf, err, s->stream);
+        cudaError_t e;
+        if (t == 3) {
+            step_coefficients(s->p, n + 2, c);
+            e = launch_step_t3_tma(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
+                                   (const float*)vbuf[vi], (float*)vbuf[1 - vi], kick_f32(a, s->rc),
+                                   kick_f32(b, s->rc), kick_f32(c, s->rc), rcf, err, s->stream);
+            if (e == cudaErrorNotSupported) {  // no tensor-map encoder: a pair, then a single step in place
+                e = launch_step_t2(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
+                                   (const float*)vbuf[vi], (float*)vbuf[1 - vi], kick_f32(a, s->rc),
+                                   kick_f32(b, s->rc), rcf, err, s->stream);
+                if (e == cudaSuccess)
+                    e = launch_step_io(s->g, s->p.precision, repro, s->phi[1 - s->cur], s->phi[s->cur],
+                                       vbuf[1 - vi], vbuf[1 - vi], &c[0], &c[1], &c[2], 1, s->rc, err, s->stream);
+                s->cur = 1 - s->cur;  // phi ends where it started; the common flip below undoes this
+            }
+        } else {
+            e = launch_step_t2(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
+                               (const float*)vbuf[vi], (float*)vbuf[1 - vi], kick_f32(a, s->rc),
+                               kick_f32(b, s->rc), rcf, err, s->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
         s->cur = 1 - s->cur;
+        vi = 1 - vi;
+        n += t;
     }
     for (int64_t k = 0; k < singles; ++k) {
         double c[5];
-        step_coefficients(s->p, s->n + 2 * pairs + k, c);
-        const void* v_in = (k == 0 && (pairs & 1)) ? s->dphi_alt : s->dphi;  // brings dphi home
+        step_coefficients(s->p, n + k, c);
+        const void* v_in = vbuf[vi];  // the first single step brings dphi home
         cudaError_t e = launch_step_io(s->g, s->p.precision, repro, s->phi[s->cur], s->phi[1 - s->cur], v_in,
                                        s->dphi, &c[0], &c[1], &c[2], 1, s->rc, err, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "prs_step launch");
         s->cur = 1 - s->cur;
+        vi = 0;
     }
-    if (swap_home) {  // dphi now sits in the second buffer, which becomes the run's own
+    if (vi) {  // dphi now sits in the second buffer, which becomes the run's own (only when swap_ok)
         void* t = s->dphi;
         s->dphi = s->dphi_alt;
         s->dphi_alt = t;

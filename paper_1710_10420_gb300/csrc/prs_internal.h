@@ -138,6 +138,14 @@ cudaError_t launch_step_t2_tma(const Geo& g, const float* phi_in, float* phi_out
                                KickF k0, KickF k1, RunConst<float> rc, unsigned int* err, cudaStream_t st,
                                float* phi_mid, float* v_mid);
 
+// Three fused leapfrog steps per pass (prs_t3tma.cu), FP32 3D boxes with an x side that is a
+// multiple of 128 and a y side that is a multiple of 8 (at least 16); dphi out of place.
+// width: the tile's columns (128 or 256; 0 picks 256 where it divides the x side).
+bool t3tma_ok(const Geo& g);
+cudaError_t launch_step_t3_tma(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
+                               KickF k0, KickF k1, KickF k2, RunConst<float> rc, unsigned int* err, cudaStream_t st,
+                               int width = 0);
+
 // Store a message for prs_last_error() on this thread.
 void record_error(const char* msg);
 

@@ -15,11 +15,13 @@ KickF kick_f32(const double coef[3], const double run_const[6])
     return KickF{(float)coef[0], (float)g, (float)(h - run_const[3] * g), (float)(h * run_const[2])};
 }
 
-// Steps one pass may fuse (params.tblock above this is clamped).
+// Steps one pass may fuse (params.tblock above this is clamped): three on the FP32 3D boxes
+// the three-step pass takes, two on the other boxes of the two-step passes.
 int max_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)repro;
-    return tblock_ok(g, precision) ? 2 : 1;
+    if (!tblock_ok(g, precision)) return 1;
+    return t3tma_ok(g) ? 3 : 2;
 }
 
 // The library's default number of steps per pass.  FP32 3D: two wherever the two-step

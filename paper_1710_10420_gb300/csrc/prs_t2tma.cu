@@ -26,6 +26,7 @@
 #include "prs_internal.h"
 #include "prs_ptx.cuh"
 #include "prs_tile.cuh"
+#include "prs_tmap.h"
 
 namespace prs {
 
@@ -51,15 +52,6 @@ static_assert(kS0 % 32 == 0 && kSV % 32 == 0 && kHL0 % 32 == 0 && kHLV % 32 == 0
 struct T2Maps {
     CUtensorMap phi12, phi10, phi2, phih, v10, v9, v1, vh;
 };
-
-__device__ __forceinline__ void tma3(float* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
 
 static __device__ __noinline__ void drain_planes(uint64_t* bar, int from, int issued, unsigned int* err)
 {
@@ -97,27 +89,27 @@ __device__ __forceinline__ void issue_plane(const Ctx& c, const T2Maps& m, int p
     if (c.tid == 0) {
         mbar_arrive_expect_tx(b, kBytesPhi + (with_v ? kBytesV : 0u));
         if (c.ywrap == 0) {
-            tma3(d0, &m.phi12, c.x0, c.y0 - 2, zg, b);
-            tma3(d0 + kHL0, &m.phih, c.xl, c.y0 - 2, zg, b);
-            tma3(d0 + kHR0, &m.phih, c.xr, c.y0 - 2, zg, b);
+            tma_load3(d0, &m.phi12, c.x0, c.y0 - 2, zg, b);
+            tma_load3(d0 + kHL0, &m.phih, c.xl, c.y0 - 2, zg, b);
+            tma_load3(d0 + kHR0, &m.phih, c.xr, c.y0 - 2, zg, b);
             if (with_v) {
-                tma3(dv, &m.v10, c.x0, c.y0 - 1, zvg, b);
-                tma3(dv + kHLV, &m.vh, c.xl, c.y0 - 1, zvg, b);
-                tma3(dv + kHRV, &m.vh, c.xr, c.y0 - 1, zvg, b);
+                tma_load3(dv, &m.v10, c.x0, c.y0 - 1, zvg, b);
+                tma_load3(dv + kHLV, &m.vh, c.xl, c.y0 - 1, zvg, b);
+                tma_load3(dv + kHRV, &m.vh, c.xr, c.y0 - 1, zvg, b);
             }
         } else if (c.ywrap < 0) {  // y0 = 0: rows ny-2, ny-1, then 0 .. 9
-            tma3(d0, &m.phi2, c.x0, c.ny - 2, zg, b);
-            tma3(d0 + 2 * kXW, &m.phi10, c.x0, 0, zg, b);
+            tma_load3(d0, &m.phi2, c.x0, c.ny - 2, zg, b);
+            tma_load3(d0 + 2 * kXW, &m.phi10, c.x0, 0, zg, b);
             if (with_v) {
-                tma3(dv, &m.v1, c.x0, c.ny - 1, zvg, b);
-                tma3(dv + kXW, &m.v9, c.x0, 0, zvg, b);
+                tma_load3(dv, &m.v1, c.x0, c.ny - 1, zvg, b);
+                tma_load3(dv + kXW, &m.v9, c.x0, 0, zvg, b);
             }
         } else {  // y0 = ny-8: rows ny-10 .. ny-1, then 0, 1
-            tma3(d0, &m.phi10, c.x0, c.ny - 10, zg, b);
-            tma3(d0 + 10 * kXW, &m.phi2, c.x0, 0, zg, b);
+            tma_load3(d0, &m.phi10, c.x0, c.ny - 10, zg, b);
+            tma_load3(d0 + 10 * kXW, &m.phi2, c.x0, 0, zg, b);
             if (with_v) {
-                tma3(dv, &m.v9, c.x0, c.ny - 9, zvg, b);
-                tma3(dv + 9 * kXW, &m.v1, c.x0, 0, zvg, b);
+                tma_load3(dv, &m.v9, c.x0, c.ny - 9, zvg, b);
+                tma_load3(dv + 9 * kXW, &m.v1, c.x0, 0, zvg, b);
             }
         }
     }
@@ -306,11 +298,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (!plane_iter<MID>(c, maps, i, issued, k0, k1, rc, am, bm, w1, hm, hc)) return;
 }
 
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+}  // namespace
 
-EncodeTiled encoder()
+EncodeTiled tmap_encoder()
 {
     static std::atomic<EncodeTiled> fn{nullptr};
     EncodeTiled f = fn.load(std::memory_order_acquire);
@@ -327,7 +317,7 @@ EncodeTiled encoder()
     return f;
 }
 
-bool encode(EncodeTiled f, CUtensorMap* m, const float* base, const Geo& g, unsigned bw, unsigned bh)
+bool tmap_encode(EncodeTiled f, CUtensorMap* m, const float* base, const Geo& g, unsigned bw, unsigned bh)
 {
     const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
     const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4};
@@ -337,8 +327,6 @@ bool encode(EncodeTiled f, CUtensorMap* m, const float* base, const Geo& g, unsi
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-
-}  // namespace
 
 // The tensor-copy pass applies to FP32 3D boxes tiled by 256 x 8 (x side a multiple of
 // 256, y side a multiple of 8 and at least 16, z side at least 3).  With a 256-wide row the
@@ -356,13 +344,13 @@ cudaError_t launch_step_t2_tma(const Geo& g, const float* phi_in, float* phi_out
 {
     if (!t2tma_ok(g)) return cudaErrorNotSupported;
     if ((((uintptr_t)phi_in | (uintptr_t)v_in) & 15u) != 0) return cudaErrorNotSupported;
-    const EncodeTiled f = encoder();
+    const EncodeTiled f = tmap_encoder();
     if (!f) return cudaErrorNotSupported;
     T2Maps m;
-    if (!encode(f, &m.phi12, phi_in, g, kXW, kR0) || !encode(f, &m.phi10, phi_in, g, kXW, 10) ||
-        !encode(f, &m.phi2, phi_in, g, kXW, 2) || !encode(f, &m.phih, phi_in, g, 4, kR0) ||
-        !encode(f, &m.v10, v_in, g, kXW, kR1) || !encode(f, &m.v9, v_in, g, kXW, 9) ||
-        !encode(f, &m.v1, v_in, g, kXW, 1) || !encode(f, &m.vh, v_in, g, 4, kR1))
+    if (!tmap_encode(f, &m.phi12, phi_in, g, kXW, kR0) || !tmap_encode(f, &m.phi10, phi_in, g, kXW, 10) ||
+        !tmap_encode(f, &m.phi2, phi_in, g, kXW, 2) || !tmap_encode(f, &m.phih, phi_in, g, 4, kR0) ||
+        !tmap_encode(f, &m.v10, v_in, g, kXW, kR1) || !tmap_encode(f, &m.v9, v_in, g, kXW, 9) ||
+        !tmap_encode(f, &m.v1, v_in, g, kXW, 1) || !tmap_encode(f, &m.vh, v_in, g, 4, kR1))
         return cudaErrorNotSupported;
     const bool mid = phi_mid != nullptr;
     const void* fn = mid ? (const void*)k_step3d_t2tma<true> : (const void*)k_step3d_t2tma<false>;

@@ -158,12 +158,30 @@ def test_tensor_copy_two_step_pass(shape, nsteps):
     assert _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
 
 
-@pytest.mark.parametrize("shape", [(256, 64, 48), (1024, 32, 24)])
-def test_two_step_passes_match_single_steps(shape):
-    """Two-step passes and one-step passes agree to FP32 rounding over many passes (3D: whole rows
-    and rows in 512-column tiles)."""
+@pytest.mark.parametrize("nsteps", [4, 7, 11])
+@pytest.mark.parametrize("shape", [(128, 16, 12), (384, 24, 9), (128, 16, 48), (512, 32, 3), (768, 16, 40),
+                                   (1024, 24, 7), (256, 48, 30)])
+def test_tensor_copy_three_step_pass(shape, nsteps):
+    """The three-step pass (x sides multiples of 128: 128-column tiles where 256 does not divide the
+    side, 256-column tiles where it does; y sides multiples of 8, at least 16): both y-wrapping
+    tiles (ny = 16: every tile wraps), x tiles at both periodic ends and inside, a whole 128- or
+    256-wide row as one tile, the minimal z side, several and uneven z chunks; passes of three
+    steps followed by a single step (4, 7) or a pair (11); fields to 1e-5 of the oracle."""
+    p = oracle.Params(shape)
+    ophi, ov = oracle.init_random(p, 31)
+    ov = 0.1 * inp.random_field(shape, 32)
+    phi, v = _run(shape, prs.PRS_FP32, nsteps, ophi.astype(np.float32), ov.astype(np.float32), seed=31, tblock=3)
+    ophi, ov = oracle.step(p, ophi, ov, nsteps)
+    assert _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
+
+
+@pytest.mark.parametrize("tblock", [2, 3])
+@pytest.mark.parametrize("shape", [(256, 64, 48), (1024, 32, 24), (384, 40, 36)])
+def test_multi_step_passes_match_single_steps(shape, tblock):
+    """Two- and three-step passes agree with one-step passes to FP32 rounding over many passes (3D:
+    whole rows, rows in 256- and 128-column tiles)."""
     a = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=1)
-    b = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=2)
+    b = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=tblock)
     assert _rel(b[0], a[0].astype(np.float64)) <= 1e-5 and _rel(b[1], a[1].astype(np.float64)) <= 1e-5
 
 
@@ -373,10 +391,11 @@ def _sampled_step_check(shape, nsteps, tblock, nsamples=48, seed=0):
     return worst
 
 
-@pytest.mark.parametrize("tblock", [0, 2])
-def test_full_size_3d_1024_sampled(tblock):
-    """3D 1024^3 FP32 (0: the benchmark's launch configuration; 2: two-step passes): sampled sites after 4 steps."""
-    worst = _sampled_step_check((1024, 1024, 1024), 4, tblock)
+@pytest.mark.parametrize("tblock,nsteps", [(0, 4), (2, 4), (3, 7)])
+def test_full_size_3d_1024_sampled(tblock, nsteps):
+    """3D 1024^3 FP32 (0: the benchmark's launch configuration; 2: two-step passes; 3: two three-step
+    passes and a single step): sampled sites after nsteps steps."""
+    worst = _sampled_step_check((1024, 1024, 1024), nsteps, tblock)
     assert worst <= 1e-5  # |phi| < 1.1: absolute ~ relative
 
 

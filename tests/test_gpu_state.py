@@ -45,45 +45,48 @@ def test_set_state_device_matches_host_upload(precision):
     assert na == nb == 12 and np.array_equal(pa, pb) and np.array_equal(va, vb)
 
 
-@pytest.mark.parametrize("shape", [(256, 32, 16), (4096, 64)])
-def test_owned_run_keeps_every_pair(shape):
-    """A run with library-owned buffers stepping by 2: every call is one two-step pass and the two
-    dphi buffers swap roles after it; the field follows the oracle and prs_device_state names the
-    buffer that holds dphi."""
-    p = prs.make_params(shape, seed=6, tblock=2)
+@pytest.mark.parametrize("shape,tblock", [((256, 32, 16), 2), ((4096, 64), 2), ((256, 32, 16), 3),
+                                          ((384, 16, 24), 3)])
+def test_owned_run_keeps_every_pass(shape, tblock):
+    """A run with library-owned buffers stepping by tblock: every call is one multi-step pass and
+    the two dphi buffers swap roles after it; the field follows the oracle and prs_device_state
+    names the buffer that holds dphi."""
+    p = prs.make_params(shape, seed=6, tblock=tblock)
     h = prs.prs_create(p)
     prs.prs_init(h)
     seen = set()
     for _ in range(5):
-        prs.prs_step(h, 2)
+        prs.prs_step(h, tblock)
         seen.add(prs.prs_device_state(h)[1])
     fshape = tuple(reversed(shape))
     phi = np.empty(fshape, np.float32)
     v = np.empty(fshape, np.float32)
     n = prs.prs_get_state(h, phi, v)
     prs.prs_destroy(h)
-    assert n == 10 and len(seen) == 2  # dphi alternated between the two buffers
+    assert n == 5 * tblock and len(seen) == 2  # dphi alternated between the two buffers
     op = oracle.Params(shape)
-    ophi, ov = oracle.step(op, *oracle.init_random(op, 6), 10)
+    ophi, ov = oracle.step(op, *oracle.init_random(op, 6), 5 * tblock)
     assert _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
 
 
-def test_bound_run_keeps_dphi_home():
-    """With bound (caller-owned) buffers dphi is in the bound buffer after every call."""
+@pytest.mark.parametrize("tblock,calls", [(2, (2, 6, 3, 4)), (3, (3, 6, 2, 4, 1, 5, 9))])
+def test_bound_run_keeps_dphi_home(tblock, calls):
+    """With bound (caller-owned) buffers dphi is in the bound buffer after every call, whatever mix
+    of multi-step passes and single steps the call's step count implies."""
     import torch
 
     shape = (256, 32, 16)
-    sim = prs.Sim(shape, seed=6, tblock=2)
+    sim = prs.Sim(shape, seed=6, tblock=tblock)
     sim.init()
     home = sim._bufs[2].data_ptr()
-    for k in (2, 6, 3, 4):
+    for k in calls:
         sim.step(k)
         assert prs.prs_device_state(sim.handle)[1] == home
     phi, v, n = sim.get_state()
     sim.close()
     op = oracle.Params(shape)
-    ophi, ov = oracle.step(op, *oracle.init_random(op, 6), 15)
-    assert n == 15 and _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
+    ophi, ov = oracle.step(op, *oracle.init_random(op, 6), sum(calls))
+    assert n == sum(calls) and _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
     torch.cuda.synchronize()
 
 

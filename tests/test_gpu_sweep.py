@@ -77,7 +77,7 @@ def _fp32_cases(n=24, seed=7):
             rb = 4096 // nx
             shape = (nx, rb * int(rng.integers(1, 5)))
         nsteps = int(rng.integers(1, 13))
-        tblock = int(rng.choice([0, 1, 2]))
+        tblock = int(rng.choice([0, 1, 2, 3]))
         cases.append((shape, nsteps, tblock, _draw_params(rng, shape, nsteps), int(rng.integers(0, 2 ** 32))))
     return cases
 
