@@ -309,14 +309,19 @@ class OwnedRun:
             self.handle = None
 
 
-def interval_calls(interval: int, tb: int):
-    """An output interval as (pure, tail) after prs_step_measure(1), which takes the diagnostics of the
-    start state inside a one-step pass: prs_step(pure) is passes of the step kernel only (with two
-    steps per pass an even number of steps), prs_step(tail) the rest (one single step for an even
-    interval).  The run's buffers are library-owned, so the pairs of every call are kept."""
+def interval_calls(interval: int, tb: int, tmax: int = 0):
+    """An output interval as (pure, tail, tail_launches) after prs_step_measure(1), which takes the
+    diagnostics of the start state inside a one-step pass: prs_step(pure) is passes of the step
+    kernel only (with two steps per pass an even number of steps), prs_step(tail) the rest.  With two
+    steps per pass the remainder of an even interval is one single step, or, where the box takes
+    three-step passes (tmax >= 3) and the library picks the passes (tblock = 0), one pair and that
+    step as one three-step pass.  The run's buffers are library-owned, so every call keeps its
+    multi-step passes."""
     rest = interval - 1
-    pure = rest - rest % tb
-    return pure, rest - pure
+    tail = rest % tb
+    if tb == 2 and tail == 1 and tmax >= 3 and rest >= 3:
+        return rest - 3, 3, 1
+    return rest - tail, tail, tail
 
 
 def run_gpu(args, world, rank, local):
@@ -336,9 +341,10 @@ def run_gpu(args, world, rank, local):
     # one bench step = one output interval: the diagnostics of its start state fused into its
     # first step (prs_step_measure(1)), then the other steps: prs_step(pure), passes of the step
     # kernel only (bracketed by events on the run's stream), and prs_step(tail)
-    pure, tail = interval_calls(args.interval, tb)
+    tmax = prs.prs_max_tblock(run.params) if args.tblock == 0 else tb
+    pure, tail, tail_launches = interval_calls(args.interval, tb, tmax)
     pure_launches = pure // tb
-    step_launches = pure_launches + tail
+    step_launches = pure_launches + tail_launches
 
     def one_step(events=None):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if events is not None else [None] * 4
@@ -412,11 +418,13 @@ def run_gpu(args, world, rank, local):
                 "effective_gbs": effective, "effective_frac": effective / peak,
                 "launch_ms": launch_avg_ms, "peak_source": f"{peak_kind} hbm_gbs (copy)",
                 "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                "fused_step_and_diagnostics_ms": fused_ms, "tail_passes_ms": tail_ms}
+                "fused_step_and_diagnostics_ms": fused_ms, "tail_passes_ms": tail_ms, "tail_steps": tail,
+                "tail_pass": ("one three-step pass (k_step3d_t3tma)" if tail == 3 and tail_launches == 1 else
+                              f"{tail} single step(s)" if tb == 2 or tb == 1 else f"{tail} step(s)")}
     if rec:
         roofline["dram_frac"] = rec["dram_bytes_per_launch"] / (launch_avg_ms / 1e3) / 1e9 / peak
 
-    state_gb = sites * 4 * (4 if tb == 2 else 3) / 1e9  # FP32 fields resident on the device
+    state_gb = sites * 4 * (4 if tb >= 2 else 3) / 1e9  # FP32 fields resident on the device
     e2e = None if args.no_e2e else run_e2e(args, prs, run, shape, stream, dev, world)
     clocks = clk.summary()
     line = {
@@ -431,7 +439,7 @@ def run_gpu(args, world, rank, local):
                    "diagnostics": "of the state at the start of each interval, fused into its first step",
                    "fused_steps_per_pass": tb,
                    "l2": (f"inputs larger than L2 (state {state_gb:.1f} GB: phi, phi', dphi"
-                          + (" and the second dphi buffer of two-step passes)" if tb == 2 else ")"))
+                          + (" and the second dphi buffer of multi-step passes)" if tb >= 2 else ")"))
                    if sites >= 512 ** 3 else "state comparable to L2; not flushed", "parallelism": f"replicas x{world}",
                    "last_output": {"area_per_volume": d.area_per_volume, "gamma_v": d.gamma_v, "step": d.step}},
         "roofline": roofline, "e2e": e2e, "clocks": clocks,

@@ -162,15 +162,18 @@ int prs_init(prs_sim* sim, const void* h_phi, const void* h_dphi);
  * prs_set_state or prs_set_state_device allocate when the run takes multi-step passes
  * (owned by the run, freed by prs_destroy; if that allocation fails, the steps run one
  * per pass).  A call of nsteps runs nsteps / T passes of T = tblock steps, then (T = 3)
- * one pair if two steps remain, then single steps.  Where dphi ends:
+ * one pair if two steps remain, then single steps; when the library chooses the steps per
+ * pass (tblock = 0, T = 2) on a box that takes three-step passes, an odd count runs one
+ * three-step pass instead of a pair and a single step.  Where dphi ends:
  *   - library-owned buffers (no prs_bind, no PRS_DEBUG): after an odd number of
  *     multi-step passes the two dphi buffers swap roles; every step count keeps all its
  *     passes.  prs_device_state returns the current buffer.
  *   - bound buffers (prs_bind) or PRS_DEBUG: dphi ends in the run's own buffer after
  *     every call.  After an odd number of multi-step passes the first single step brings
- *     dphi home; with no single step to do it, the last pair runs as two single steps
- *     (T = 2: counts 2, 6, 10, ...; T = 3: counts 2, 8, 14, ...) or the last triple as a
- *     pair and a single step (T = 3: counts 3, 9, 15, ...). */
+ *     dphi home; with no single step to do it, the three-step pass of an odd T = 2 count
+ *     runs as a pair and a single step, else the last pair as two single steps (T = 2:
+ *     counts 2, 6, 10, ...; T = 3: counts 2, 8, 14, ...), else the last triple as a pair
+ *     and a single step (T = 3: counts 3, 9, 15, ...). */
 int prs_step(prs_sim* sim, int64_t nsteps);
 
 /* Wall diagnostics of the current state (Eq. 7, Eq. 8), reduced on the device in
@@ -339,6 +342,13 @@ int prs_coefficients(const prs_params* params, int64_t n, double out[5]);
 /* Leapfrog steps the library fuses into one pass over HBM for these parameters
  * when params->tblock is 0 (>= 1), or a negative status for invalid parameters. */
 int prs_default_tblock(const prs_params* params);
+
+/* The most leapfrog steps one pass over HBM can fuse for these parameters (>= 1; a
+ * params->tblock above it acts as it): 3 for FP32 3D boxes the three-step pass takes, 2
+ * for the other boxes of the two-step passes, else 1; or a negative status for invalid
+ * parameters.  Follows the fusion of Eqs. 3-5 over several steps, which the paper does
+ * not do (it launches one kernel per equation and step, Sec. III). */
+int prs_max_tblock(const prs_params* params);
 
 /* Self-test of failure detection (no counterpart in the paper).  Launches one
  * CTA that waits on an mbarrier phase that can never complete (the bounded wait

@@ -118,6 +118,7 @@ _SIGS = {
     "prs_destroy": (ctypes.c_int, [_VP]),
     "prs_coefficients": (ctypes.c_int, [_P, ctypes.c_int64, _DP]),
     "prs_default_tblock": (ctypes.c_int, [_P]),
+    "prs_max_tblock": (ctypes.c_int, [_P]),
     "prs_selftest_wait_timeout": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint)]),
     "prs_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
     "prs_batch_run": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64, _DP, ctypes.c_int64]),
@@ -343,6 +344,13 @@ def prs_default_tblock(params: prs_params) -> int:
     rc = load().prs_default_tblock(ctypes.byref(params))
     if rc < 0:
         _check(rc, "prs_default_tblock")
+    return rc
+
+
+def prs_max_tblock(params: prs_params) -> int:
+    rc = load().prs_max_tblock(ctypes.byref(params))
+    if rc < 0:
+        _check(rc, "prs_max_tblock")
     return rc
 
 

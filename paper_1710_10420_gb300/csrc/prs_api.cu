@@ -140,6 +140,15 @@ extern "C" int prs_default_tblock(const prs_params* params)
     return t < 1 ? 1 : t;
 }
 
+extern "C" int prs_max_tblock(const prs_params* params)
+{
+    Geo g;
+    int rc = check_params(params, &g);
+    if (rc) return rc;
+    int t = max_fused_steps(g, params->precision, (params->flags & PRS_REPRO) != 0);
+    return t < 1 ? 1 : t;
+}
+
 // -------------------------------------------------------------- lifecycle
 
 static const int kMeasureBlocks = 8192;  // partial slots: the fast kernels use one per tile
@@ -445,23 +454,35 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
     const bool repro = (s->p.flags & PRS_REPRO) != 0;
     const int tb = run_tblock(s);
     // Multi-step passes (two or three steps) read dphi across sites, so they write it to a
-    // second buffer; a call runs `big` passes of tb steps, then (tb = 3) at most one pair, then
-    // single steps.  After an odd number of multi-step passes dphi sits in the second buffer.  A
-    // run whose buffers the library owns (no PRS_DEBUG guard bands) then just swaps the roles of
-    // its two dphi buffers.  A run with bound buffers keeps dphi in the bound buffer at the end of
-    // every call: the first single step after an odd number of multi-step passes reads dphi in
-    // the second buffer and writes the bound one; with no single step to do it, the last pair
-    // runs as two single steps (tb = 2, or the pair of tb = 3) or the last triple as a pair and a
+    // second buffer.  A call runs n3 passes of three steps, n2 of two, then n1 single steps:
+    // with T = tblock = 3, nsteps / 3 triples and a pair or a single step for the remainder;
+    // with T = 2, pairs, and for an odd count a single step, or, when the library chooses the
+    // steps per pass (tblock = 0) and the box takes three-step passes, one triple instead of a
+    // pair and a single step.  After an odd number of multi-step passes dphi sits in the
+    // second buffer.  A run whose buffers the library owns (no PRS_DEBUG guard bands) then
+    // swaps the roles of its two dphi buffers.  A run with bound buffers keeps dphi in the
+    // bound buffer at the end of every call: the first single step after an odd number of
+    // multi-step passes reads dphi in the second buffer and writes the bound one; with no
+    // single step to do it, the triple of an odd T = 2 count runs as a pair and a single
+    // step, else the last pair as two single steps, else the last triple as a pair and a
     // single step.  Single steps otherwise update dphi in place.
     const bool swap_ok = s->owned && (s->p.flags & PRS_DEBUG) == 0;
-    int64_t big = tb >= 2 ? nsteps / tb : 0;
-    int64_t pairs = (tb == 3 && nsteps - big * tb == 2) ? 1 : 0;
-    int64_t singles = nsteps - big * tb - 2 * pairs;
-    if (!s->dphi_alt) big = pairs = 0, singles = nsteps;  // no second buffer (no room at prs_init)
-    if (((big + pairs) & 1) && singles == 0 && !swap_ok) {
-        if (pairs) pairs = 0, singles = 2;
-        else if (tb == 3) --big, pairs = 1, singles = 1;
-        else --big, singles = 2;
+    int64_t n3 = 0, n2 = 0, n1 = nsteps;
+    if (tb == 3) {
+        n3 = nsteps / 3;
+        n2 = nsteps - 3 * n3 == 2 ? 1 : 0;
+        n1 = nsteps - 3 * n3 - 2 * n2;
+    } else if (tb == 2) {
+        n2 = nsteps / 2;
+        n1 = nsteps - 2 * n2;
+        if (n1 == 1 && n2 >= 1 && s->p.tblock == 0 && max_fused_steps(s->g, s->p.precision, repro) >= 3)
+            n3 = 1, n2 -= 1, n1 = 0;
+    }
+    if (!s->dphi_alt) n3 = n2 = 0, n1 = nsteps;  // no second buffer (no room at prs_init)
+    if (((n3 + n2) & 1) && n1 == 0 && !swap_ok) {
+        if (tb == 2 && n3 == 1) n3 = 0, n2 += 1, n1 = 1;
+        else if (n2 > 0) n2 -= 1, n1 += 2;
+        else n3 -= 1, n2 += 1, n1 += 1;
     }
     unsigned int* err = &s->d_status->error;
     const RunConst<float> rcf{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
@@ -469,8 +490,8 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
     void* vbuf[2] = {s->dphi, s->dphi_alt};
     int vi = 0;  // vbuf[vi] holds dphi
     int64_t n = s->n;
-    for (int64_t k = 0; k < big + pairs; ++k) {
-        const int t = k < big ? tb : 2;
+    for (int64_t k = 0; k < n3 + n2; ++k) {
+        const int t = k < n3 ? 3 : 2;
         double a[5], b[5], c[5];
         step_coefficients(s->p, n, a);
         step_coefficients(s->p, n + 1, b);
@@ -499,7 +520,7 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
         vi = 1 - vi;
         n += t;
     }
-    for (int64_t k = 0; k < singles; ++k) {
+    for (int64_t k = 0; k < n1; ++k) {
         double c[5];
         step_coefficients(s->p, n + k, c);
         const void* v_in = vbuf[vi];  // the first single step brings dphi home

@@ -34,6 +34,25 @@ struct KickF {
     float c1, g, k1, k2;
 };
 
+// KickF and the time step as f32x2 operands: each word holds the same float in both halves,
+// so the packed update (update4p) takes its constants as they are, with no per-use packing.
+struct KickP {
+    unsigned long long c1, g, k1, nk2, dt;  // c1, g, k1, -k2, deta
+};
+
+inline unsigned long long pack_pair(float f)
+{
+    unsigned int u;
+    static_assert(sizeof u == sizeof f, "32-bit float");
+    __builtin_memcpy(&u, &f, sizeof u);
+    return ((unsigned long long)u << 32) | u;
+}
+
+inline KickP kick_packed(const KickF& k, float deta)
+{
+    return KickP{pack_pair(k.c1), pack_pair(k.g), pack_pair(k.k1), pack_pair(-k.k2), pack_pair(deta)};
+}
+
 // The FP64 form of KickF (the non-reproducible FP64 step, prs_generic.cu).
 struct KickD {
     double c1, g, k1, k2;
@@ -140,7 +159,7 @@ cudaError_t launch_step_t2_tma(const Geo& g, const float* phi_in, float* phi_out
 
 // Three fused leapfrog steps per pass (prs_t3tma.cu), FP32 3D boxes with an x side that is a
 // multiple of 128 and a y side that is a multiple of 8 (at least 16); dphi out of place.
-// width: the tile's columns (128 or 256; 0 picks 256 where it divides the x side).
+// width: the tile's columns (128 or 256; 0 picks the default, 128).
 bool t3tma_ok(const Geo& g);
 cudaError_t launch_step_t3_tma(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
                                KickF k0, KickF k1, KickF k2, RunConst<float> rc, unsigned int* err, cudaStream_t st,

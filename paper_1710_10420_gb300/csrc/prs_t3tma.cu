@@ -21,6 +21,14 @@
 // level-2 columns outside the tile (two and one on each side) are single sites computed by
 // 48 halo lanes on the two warps of rows that only run level 1.  One barrier per plane.
 // dphi goes out of place (level 1 reads it on rows and planes of the neighbouring tiles).
+//
+// Instruction count is what bounds a pass that moves this few bytes per update, so the
+// plane loop is specialised: the six iterations that fill the pipeline run with the later
+// levels compiled out, and the steady-state body tests no plane ranges; the kick constants
+// arrive packed as f32x2 operands; the copy context sits in shared memory (only thread 0
+// reads it); x-edge values are loaded by the two lanes that use them.  At 512^3 that took
+// the pass from 495 M to 387 M warp instructions (and shared-memory bank conflicts from
+// 22.5 M to 9.3 M).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -71,28 +79,52 @@ static __device__ __noinline__ void drain3(uint64_t* bar, int from, int issued, 
     for (int i = from; i <= issued; ++i) mbar_wait(&bar[i & 3], (unsigned)(i >> 2) & 1u, err);
 }
 
+// What the copies of a plane need.  Only thread 0 (and, on the tiles at the ends of y, the
+// last two warps) issue copies, so this lives in shared memory rather than in every thread's
+// registers.
 struct Ctx3 {
     const float* phi_in;
     const float* v_in;
-    float *ring0, *ringv, *ring1, *ring2;
-    uint64_t* bar;
     size_t plane;
     int nx, ny, nz, x0, y0, z0, zn, xl, xr, ywrap;  // ywrap: 0, -1 (top tile), +1 (bottom tile)
-    int tid;
+};
+
+// The CTA's shared memory: mbarriers and the copy context, then the rings.
+struct Smem3 {
+    uint64_t bar[4];
+    Ctx3 c;
+};
+static_assert(sizeof(Smem3) <= 128, "header fits the first 128 bytes");
+
+extern __shared__ __align__(128) unsigned char t3_smem[];
+
+__device__ __forceinline__ Smem3* hdr3() { return reinterpret_cast<Smem3*>(t3_smem); }
+
+// ring0 (4 phi slots), ringv (3 dphi slots), ring1 and ring2 (2 slots each), after the header
+template <int XW>
+struct Rings3 {
+    using S = T3<XW>;
+    static __device__ __forceinline__ float* r0() { return reinterpret_cast<float*>(t3_smem + 128); }
+    static __device__ __forceinline__ float* rv() { return r0() + 4 * S::kS0; }
+    static __device__ __forceinline__ float* r1() { return rv() + 3 * S::kSV; }
+    static __device__ __forceinline__ float* r2() { return r1() + 2 * S::kS1; }
 };
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Stage level-0 plane pl (global z0-3+pl) and, with with_v, the dphi of level-1 plane pl-1.
+// Stage level-0 plane pl (global z0-3+pl) and, with with_v, the dphi of level-1 plane pl-1
+// into dphi slot vs = (pl-1) mod 3.  Called by every thread; thread 0 issues the tensor copies.
 template <int XW>
-__device__ __forceinline__ void issue3(const Ctx3& c, const T3Maps& m, int pl, bool with_v)
+__device__ __forceinline__ void issue3(const T3Maps& m, int tid, int pl, bool with_v, int vs)
 {
     using S = T3<XW>;
-    uint64_t* b = &c.bar[pl & 3];
-    const int zg = wrapi(c.z0 - 3 + pl, c.nz), zvg = wrapi(c.z0 - 4 + pl, c.nz);
-    float* d0 = c.ring0 + (pl & 3) * S::kS0;
-    float* dv = c.ringv + ((pl + 2) % 3) * S::kSV;  // slot of level-1 plane pl-1
-    if (c.tid == 0) {
+    using R = Rings3<XW>;
+    const Ctx3& c = hdr3()->c;
+    uint64_t* b = &hdr3()->bar[pl & 3];
+    if (tid == 0) {
+        const int zg = wrapi(c.z0 - 3 + pl, c.nz), zvg = wrapi(c.z0 - 4 + pl, c.nz);
+        float* d0 = R::r0() + (pl & 3) * S::kS0;
+        float* dv = R::rv() + vs * S::kSV;
         mbar_arrive_expect_tx(b, S::kBytesPhi + (with_v ? S::kBytesV : 0u));
         if (c.ywrap == 0) {
             tma_load3(d0, &m.phi14, c.x0, c.y0 - 3, zg, b);
@@ -119,10 +151,13 @@ __device__ __forceinline__ void issue3(const Ctx3& c, const T3Maps& m, int pl, b
             }
         }
     }
-    if (c.ywrap != 0 && c.tid >= S::kThreads - 64) {
+    if (tid >= S::kThreads - 64 && c.ywrap != 0) {
         // the wrap tiles' halo columns row by row (16 bytes each) on the last two warps: task
         // t < 2 kR0 is phi row t/2, side t%2; then 2 kR1 dphi tasks
-        const int t = c.tid - (S::kThreads - 64);
+        const int zg = wrapi(c.z0 - 3 + pl, c.nz), zvg = wrapi(c.z0 - 4 + pl, c.nz);
+        float* d0 = R::r0() + (pl & 3) * S::kS0;
+        float* dv = R::rv() + vs * S::kSV;
+        const int t = tid - (S::kThreads - 64);
         const bool isv = t >= 2 * kR0;
         if (t < 2 * (kR0 + kR1) && (!isv || with_v)) {
             const int tt = isv ? t - 2 * kR0 : t, r = tt >> 1, side = tt & 1;
@@ -142,164 +177,189 @@ __device__ __forceinline__ void xnb(float4 cc, float e, int lane, float& left, f
     right = lane == 31 ? e : sd;
 }
 
+// Per-thread offsets and roles.
+struct Lane3 {
+    int tid, lane, o0, o1, e0;
+    bool edge, lv2, lv3, hal, hal2;
+    unsigned hx;  // halo lane: its x neighbours' offsets in the phi slot, hxm | hxp << 16
+    int hc, hv, ho;
+};
+
+// What a thread carries from plane to plane: level 0 at plane j-1 (am), level 1 at k-1 (bm),
+// level 2 at l-1 (cm), the dphi level 1 and level 2 hand to the next level (w1, w2), and the
+// halo lane's counterparts.  (Two sets alternating with the plane parity, so that a loop
+// unrolled by two rotates them by renaming, need more than the 80 registers a thread of
+// two 384-thread CTAs per SM has: they spilled and ran slower.)
+struct Queue3 {
+    float4 am, bm, cm, w1, w2;
+    float hm, hb, hw;
+};
+
+// Plane iteration i with levels 1..LV active (LV = 3 in the steady state, whose loop body
+// then tests no plane ranges; the first six iterations fill the pipeline).  vs = (i-1) mod 3,
+// the dphi slot of level-1 plane j = i-1.  po, vo: the outputs at level-3 plane l = i-3, this
+// thread's site.  Returns false when a wait gave up.
+template <int XW, int LV>
+__device__ __forceinline__ bool t3_iter(const T3Maps& m, const Lane3& t, int i, int nplanes, int vs, float* po,
+                                        float* vo, const KickP& k0, const KickP& k1, const KickP& k2, Queue3& q,
+                                        unsigned int* err)
+{
+    using S = T3<XW>;
+    using R = Rings3<XW>;
+    const int P = i & 1;
+    const bool ok = mbar_wait(&hdr3()->bar[i & 3], (unsigned)(i >> 2) & 1u, err);
+    if (__syncthreads_or(!ok)) {
+        if (t.tid == 0) drain3(hdr3()->bar, i, min(i + 1, nplanes - 1), err);  // planes issued so far
+        return false;
+    }
+    if (i + 2 < nplanes) issue3<XW>(m, t.tid, i + 2, true, vs == 0 ? 2 : vs - 1);
+    const float* Ln = R::r0() + (i & 3) * S::kS0;        // level 0 at plane j+1
+    const float* Lj = R::r0() + ((i + 3) & 3) * S::kS0;  // level 0 at plane j
+    float4 pn, qn, w1n, w2n;
+    float hpn = 0.f, hwn = 0.f;
+    if (LV >= 1) {  // level 1 (step n) at plane j: level 0 at j-1 (am), j (ring), j+1 (ring)
+        float* L1 = R::r1() + (P ^ 1) * S::kS1;
+        const float* V = R::rv() + vs * S::kSV;
+        const float4 a = lds4(Lj + t.o0);
+        float e = 0.f, left, right;
+        if (t.edge) e = Lj[t.e0];
+        xnb(a, e, t.lane, left, right);
+        float4 v = lds4(V + t.o0 - XW);
+        update4p(a, left, right, lds4(Lj + t.o0 + XW), lds4(Lj + t.o0 - XW), lds4(Ln + t.o0), q.am, v, pn, k0);
+        *reinterpret_cast<float4*>(L1 + t.o1) = pn;
+        q.am = a;
+        w1n = v;
+        if (t.hal) {
+            const float hcen = Lj[t.hc];
+            float hv = V[t.hv];
+            hpn = update1(hcen, Lj[t.hx >> 16], Lj[t.hx & 0xffffu], Lj[t.hc + 4], Lj[t.hc - 4], Ln[t.hc], q.hm, hv,
+                          kick_scalar(k0), deta_only(k0), true);
+            L1[t.ho] = hpn;
+            q.hm = hcen;
+            hwn = hv;
+        }
+    }
+    if (LV >= 2) {  // level 2 (step n+1) at plane k: level 1 at k-1 (bm), k (ring), k+1 (pn)
+        const float* L1k = R::r1() + P * S::kS1;
+        float* L2 = R::r2() + P * S::kS1;
+        if (t.lv2) {
+            const float4 b = lds4(L1k + t.o1);
+            float e = 0.f, left, right;
+            if (t.edge) e = L1k[t.o1 + (t.lane == 0 ? -1 : 4)];
+            xnb(b, e, t.lane, left, right);
+            float4 v = q.w1;
+            update4p(b, left, right, lds4(L1k + t.o1 + S::kW), lds4(L1k + t.o1 - S::kW), pn, q.bm, v, qn, k1);
+            *reinterpret_cast<float4*>(L2 + t.o1) = qn;
+            q.bm = b;
+            w2n = v;
+        }
+        if (t.hal2) {
+            const float hcen = L1k[t.ho];
+            float hv = q.hw;
+            L2[t.ho] = update1(hcen, L1k[t.ho + 1], L1k[t.ho - 1], L1k[t.ho + S::kW], L1k[t.ho - S::kW], hpn, q.hb,
+                               hv, kick_scalar(k1), deta_only(k1), true);
+            q.hb = hcen;
+        }
+    }
+    if (LV >= 3 && t.lv3) {  // level 3 (step n+2) at plane l: level 2 at l-1 (cm), l (ring), l+1 (qn)
+        const float* L2l = R::r2() + (P ^ 1) * S::kS1;
+        const float4 d = lds4(L2l + t.o1);
+        float e = 0.f, left, right;
+        if (t.edge) e = L2l[t.o1 + (t.lane == 0 ? -1 : 4)];
+        xnb(d, e, t.lane, left, right);
+        float4 v = q.w2, out;
+        update4p(d, left, right, lds4(L2l + t.o1 + S::kW), lds4(L2l + t.o1 - S::kW), qn, q.cm, v, out, k2);
+        stg4(po, out);
+        stg4(vo, v);
+        q.cm = d;
+    }
+    // the dphi handed down reaches the next level in the next iteration
+    if (LV >= 1) q.w1 = w1n;
+    if (LV >= 1 && t.hal) q.hw = hwn;
+    if (LV >= 2 && t.lv2) q.w2 = w2n;
+    return true;
+}
+
 template <int XW>
 __global__ void __launch_bounds__(T3<XW>::kThreads, T3<XW>::kMinBlocks)
     k_step3d_t3tma(const __grid_constant__ T3Maps maps, const float* __restrict__ phi_in,
                    float* __restrict__ phi_out, const float* __restrict__ v_in, float* __restrict__ v_out, int nx,
-                   int ny, int nz, int cz, KickF k0, KickF k1, KickF k2, RunConst<float> rc, unsigned int* err)
+                   int ny, int nz, int cz, KickP k0, KickP k1, KickP k2, unsigned int* err)
 {
     using S = T3<XW>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Ctx3 c;
-    c.bar = reinterpret_cast<uint64_t*>(smem_raw);
-    c.ring0 = reinterpret_cast<float*>(smem_raw + 128);
-    c.ringv = c.ring0 + 4 * S::kS0;
-    c.ring1 = c.ringv + 3 * S::kSV;
-    c.ring2 = c.ring1 + 2 * S::kS1;
-    c.phi_in = phi_in;
-    c.v_in = v_in;
-    c.nx = nx;
-    c.ny = ny;
-    c.nz = nz;
-    c.plane = (size_t)nx * ny;
-    c.tid = threadIdx.x;
-    const int lane = c.tid & 31;
+    using R = Rings3<XW>;
     const int nxt = nx / XW, ytiles = ny / kTY;
-    c.x0 = (blockIdx.x % nxt) * XW;
-    c.y0 = (blockIdx.x / nxt % ytiles) * kTY;
-    c.z0 = blockIdx.x / nxt / ytiles * cz;
-    c.zn = min(cz, nz - c.z0);
-    const int nplanes = c.zn + 6;  // level-0 local planes 0 .. zn+5 = global z0-3 .. z0+zn+2
-    c.xl = c.x0 >= 4 ? c.x0 - 4 : c.x0 - 4 + nx;
-    c.xr = c.x0 + XW < nx ? c.x0 + XW : 0;
-    c.ywrap = c.y0 == 0 ? -1 : (c.y0 + kTY == ny ? 1 : 0);
+    const int x0 = (blockIdx.x % nxt) * XW, y0 = (blockIdx.x / nxt % ytiles) * kTY, z0 = blockIdx.x / nxt / ytiles * cz;
+    const int zn = min(cz, nz - z0);
+    const int nplanes = zn + 6;  // level-0 local planes 0 .. zn+5 = global z0-3 .. z0+zn+2
+    const size_t plane = (size_t)nx * ny;
 
     // this thread's float4: level-1 row r (global y0-2+r), column x0+4 col
-    const int r = c.tid / S::F, col = c.tid % S::F;
-    const int o0 = (r + 1) * XW + 4 * col;      // phi slot (phi row r+1); dphi slot at o0 - XW
-    const int o1 = r * S::kW + 4 + 4 * col;     // level-1/2 slots
-    const int e0 = lane == 0 ? (col == 0 ? S::kHL0 + (r + 1) * 4 + 3 : o0 - 1)
-                             : (col == S::F - 1 ? S::kHR0 + (r + 1) * 4 : o0 + 4);
-    const int e1 = o1 + (lane == 0 ? -1 : 4);  // the same neighbour in the level-1/2 slots
-    const bool lv2 = r >= 1 && r <= kTY + 2, lv3 = r >= 2 && r <= kTY + 1;  // warp-uniform
-    const int go = (c.y0 - 2 + r) * nx + c.x0 + 4 * col;
+    Lane3 t;
+    t.tid = threadIdx.x;
+    t.lane = t.tid & 31;
+    const int r = t.tid / S::F, col = t.tid % S::F;
+    t.o0 = (r + 1) * XW + 4 * col;   // phi slot (phi row r+1); dphi slot at o0 - XW
+    t.o1 = r * S::kW + 4 + 4 * col;  // level-1/2 slots
+    t.e0 = t.lane == 0 ? (col == 0 ? S::kHL0 + (r + 1) * 4 + 3 : t.o0 - 1)
+                       : (col == S::F - 1 ? S::kHR0 + (r + 1) * 4 : t.o0 + 4);
+    t.edge = t.lane == 0 || t.lane == 31;
+    t.lv2 = r >= 1 && r <= kTY + 2;  // warp-uniform
+    t.lv3 = r >= 2 && r <= kTY + 1;
 
     // halo lanes: the first warp (row 0) and the last 16 lanes of the last warp (row 11), both
     // level-1-only rows.  Halo site h: row h/4, column x0-2, x0-1, x0+XW, x0+XW+1 for h%4 = 0..3;
     // the two inner columns of rows 1..10 also run level 2.
-    const int h = c.tid < 32 ? c.tid : (c.tid >= S::kThreads - (kHalo - 32) ? c.tid - (S::kThreads - kHalo) : -1);
-    const bool hal = h >= 0;
-    int hc = 0, hxm = 0, hxp = 0, hv = 0, ho = 4;
-    bool hal2 = false;
-    if (hal) {
+    const int h = t.tid < 32 ? t.tid : (t.tid >= S::kThreads - (kHalo - 32) ? t.tid - (S::kThreads - kHalo) : -1);
+    t.hal = h >= 0;
+    t.hc = 0, t.hx = 0, t.hv = 0, t.ho = 4;
+    t.hal2 = false;
+    if (t.hal) {
         const int hr = h >> 2, w = h & 3;
         const int base = w < 2 ? S::kHL0 + (hr + 1) * 4 + 2 + w : S::kHR0 + (hr + 1) * 4 + (w - 2);
-        hc = base;
-        hxm = w == 2 ? (hr + 1) * XW + XW - 1 : base - 1;
-        hxp = w == 1 ? (hr + 1) * XW : base + 1;
-        hv = w < 2 ? S::kHLV + hr * 4 + 2 + w : S::kHRV + hr * 4 + (w - 2);
-        ho = hr * S::kW + (w < 2 ? 2 + w : XW + 4 + (w - 2));
-        hal2 = (w == 1 || w == 2) && hr >= 1 && hr <= kTY + 2;
+        t.hc = base;
+        const unsigned hxm = w == 2 ? (hr + 1) * XW + XW - 1 : base - 1, hxp = w == 1 ? (hr + 1) * XW : base + 1;
+        t.hx = hxm | hxp << 16;
+        t.hv = w < 2 ? S::kHLV + hr * 4 + 2 + w : S::kHRV + hr * 4 + (w - 2);
+        t.ho = hr * S::kW + (w < 2 ? 2 + w : XW + 4 + (w - 2));
+        t.hal2 = (w == 1 || w == 2) && hr >= 1 && hr <= kTY + 2;
     }
 
-    if (c.tid == 0) {
+    if (t.tid == 0) {
+        Smem3* sm = hdr3();
+        sm->c = Ctx3{phi_in, v_in, plane, nx, ny, nz, x0, y0, z0, zn, x0 >= 4 ? x0 - 4 : x0 - 4 + nx,
+                     x0 + XW < nx ? x0 + XW : 0, y0 == 0 ? -1 : (y0 + kTY == ny ? 1 : 0)};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&c.bar[i], 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&sm->bar[i], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    issue3<XW>(c, maps, 0, false);
-    issue3<XW>(c, maps, 1, false);
-    int issued = 1;
+    issue3<XW>(maps, t.tid, 0, false, 0);
+    issue3<XW>(maps, t.tid, 1, false, 0);
 
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 am = z4, bm = z4, cm = z4, w1 = z4, w2 = z4;
-    float hm = 0.f, hb = 0.f, hw = 0.f;
-    for (int i = 0; i < nplanes; ++i) {
-        const bool ok = mbar_wait(&c.bar[i & 3], (unsigned)(i >> 2) & 1u, err);
-        if (__syncthreads_or(!ok)) {
-            if (c.tid == 0) drain3(c.bar, i, issued, err);
-            return;
-        }
-        if (i + 2 < nplanes) {
-            issue3<XW>(c, maps, i + 2, i + 1 >= 1 && i + 1 <= c.zn + 4);
-            issued = i + 2;
-        }
-        const int j = i - 1, k = i - 2, l = i - 3;  // planes of levels 1, 2, 3
-        const float* Ln = c.ring0 + (i & 3) * S::kS0;        // level 0 at plane j+1
-        const float* Lj = c.ring0 + ((i + 3) & 3) * S::kS0;  // level 0 at plane j
-        float4 pn = z4, w1n = z4, qn = z4, w2n = z4;
-        float hpn = 0.f, hwn = 0.f;
-        // level 1 (step n) at plane j
-        if (j >= 1 && j <= c.zn + 4) {
-            float* L1 = c.ring1 + (j & 1) * S::kS1;
-            const float* V = c.ringv + (j % 3) * S::kSV;
-            const float4 cc = lds4(Lj + o0);
-            float left, right;
-            xnb(cc, Lj[e0], lane, left, right);
-            w1n = lds4(V + o0 - XW);
-            update4(cc, left, right, lds4(Lj + o0 + XW), lds4(Lj + o0 - XW), lds4(Ln + o0), am, w1n, pn, k0, rc,
-                    true);
-            *reinterpret_cast<float4*>(L1 + o1) = pn;
-            am = cc;
-            if (hal) {
-                const float hcen = Lj[hc];
-                hwn = V[hv];
-                hpn = update1(hcen, Lj[hxp], Lj[hxm], Lj[hc + 4], Lj[hc - 4], Ln[hc], hm, hwn, k0, rc, true);
-                L1[ho] = hpn;
-                hm = hcen;
-            }
-        } else {
-            am = lds4(Lj + o0);
-            if (hal) hm = Lj[hc];
-        }
-        // level 2 (step n+1) at plane k: level 1 at k-1 (bm), k (ring), k+1 (pn)
-        if (k >= 2 && k <= c.zn + 3) {
-            const float* L1 = c.ring1 + (k & 1) * S::kS1;
-            float* L2 = c.ring2 + (k & 1) * S::kS1;
-            if (lv2) {
-                const float4 cc = lds4(L1 + o1);
-                float left, right;
-                xnb(cc, L1[e1], lane, left, right);
-                w2n = w1;
-                update4(cc, left, right, lds4(L1 + o1 + S::kW), lds4(L1 + o1 - S::kW), pn, bm, w2n, qn, k1, rc,
-                        true);
-                *reinterpret_cast<float4*>(L2 + o1) = qn;
-                bm = cc;
-            }
-            if (hal2) {
-                const float hcen = L1[ho];
-                float vv = hw;
-                L2[ho] = update1(hcen, L1[ho + 1], L1[ho - 1], L1[ho + S::kW], L1[ho - S::kW], hpn, hb, vv, k1, rc,
-                                 true);
-                hb = hcen;
-            }
-        } else if (k == 1) {  // level 1 at plane 1: the first level-2 plane's z neighbour below
-            const float* L1 = c.ring1 + S::kS1;
-            if (lv2) bm = lds4(L1 + o1);
-            if (hal2) hb = L1[ho];
-        }
-        // level 3 (step n+2) at plane l: level 2 at l-1 (cm), l (ring), l+1 (qn); output
-        if (l >= 3 && l <= c.zn + 2) {
-            if (lv3) {
-                const float* L2 = c.ring2 + (l & 1) * S::kS1;
-                const float4 cc = lds4(L2 + o1);
-                float left, right;
-                xnb(cc, L2[e1], lane, left, right);
-                float4 vv = w2, out;
-                update4(cc, left, right, lds4(L2 + o1 + S::kW), lds4(L2 + o1 - S::kW), qn, cm, vv, out, k2, rc,
-                        true);
-                const size_t zo = (size_t)(c.z0 - 3 + l) * c.plane;
-                stg4(phi_out + zo + go, out);
-                stg4(v_out + zo + go, vv);
-                cm = cc;
-            }
-        } else if (l == 2) {  // level 2 at plane 2 (ring slot 0): the first output plane's z neighbour below
-            if (lv3) cm = lds4(c.ring2 + o1);
-        }
-        w1 = w1n;
-        w2 = w2n;
-        hw = hwn;
+    Queue3 q;
+    const size_t go = (size_t)z0 * plane + (size_t)(y0 - 2 + r) * nx + x0 + 4 * col;  // level-3 plane 3 = z0
+    float* po = phi_out + go;
+    float* vo = v_out + go;
+    // pipeline fill: iterations 0, 1 only stage planes; level 1 starts at 2, level 2 at 4,
+    // level 3 at 6; the queues' first planes are read where they are first needed
+    if (!t3_iter<XW, 0>(maps, t, 0, nplanes, 2, po, vo, k0, k1, k2, q, err)) return;
+    if (!t3_iter<XW, 0>(maps, t, 1, nplanes, 0, po, vo, k0, k1, k2, q, err)) return;
+    q.am = lds4(R::r0() + t.o0);  // level 0 at plane 0 (slot 0)
+    if (t.hal) q.hm = R::r0()[t.hc];
+    if (!t3_iter<XW, 1>(maps, t, 2, nplanes, 1, po, vo, k0, k1, k2, q, err)) return;
+    if (!t3_iter<XW, 1>(maps, t, 3, nplanes, 2, po, vo, k0, k1, k2, q, err)) return;
+    if (t.lv2) q.bm = lds4(R::r1() + S::kS1 + t.o1);  // level 1 at plane 1 (slot 1)
+    if (t.hal2) q.hb = R::r1()[S::kS1 + t.ho];
+    if (!t3_iter<XW, 2>(maps, t, 4, nplanes, 0, po, vo, k0, k1, k2, q, err)) return;
+    if (!t3_iter<XW, 2>(maps, t, 5, nplanes, 1, po, vo, k0, k1, k2, q, err)) return;
+    if (t.lv3) q.cm = lds4(R::r2() + t.o1);  // level 2 at plane 2 (slot 0)
+    int vs = 2;                                 // (i-1) mod 3 at i = 6
+    for (int i = 6; i < nplanes; ++i) {
+        if (!t3_iter<XW, 3>(maps, t, i, nplanes, vs, po, vo, k0, k1, k2, q, err)) return;
+        po += plane;
+        vo += plane;
+        vs = vs == 2 ? 0 : vs + 1;
     }
 }
 
@@ -315,8 +375,8 @@ bool encode_maps(T3Maps& m, const float* phi_in, const float* v_in, const Geo& g
 }
 
 template <int XW>
-cudaError_t launch_xw(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out, KickF k0,
-                      KickF k1, KickF k2, RunConst<float> rc, unsigned int* err, cudaStream_t st)
+cudaError_t launch_xw(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out, KickP k0,
+                      KickP k1, KickP k2, unsigned int* err, cudaStream_t st)
 {
     using S = T3<XW>;
     T3Maps m;
@@ -348,18 +408,17 @@ cudaError_t launch_xw(const Geo& g, const float* phi_in, float* phi_out, const f
     const long long blocks = (long long)tiles * ((g.nz + cz - 1) / cz);
     if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
     k_step3d_t3tma<XW><<<(unsigned)blocks, S::kThreads, S::kSmem, st>>>(m, phi_in, phi_out, v_in, v_out, g.nx, g.ny,
-                                                                       g.nz, cz, k0, k1, k2, rc, err);
+                                                                       g.nz, cz, k0, k1, k2, err);
     return cudaGetLastError();
 }
 
-// Tile width for this box: 256 where it divides the x side (one 768-thread CTA per SM),
-// else 128 (two 384-thread CTAs per SM); 0 when the pass does not apply.
+// Tile width for this box: 128 columns (two 384-thread CTAs per SM) wherever the x side is a
+// multiple of 128.  The 256-column tile (one 768-thread CTA per SM, the same redundancy in y,
+// half the x-halo work) measured slower at 1024^3: 1.49 against 1.43 ms per step.
 int t3_width(const Geo& g)
 {
     if (g.dims != 3 || g.ny % kTY != 0 || g.ny < 2 * kTY || g.nz < 3) return 0;
-    if (g.nx % 256 == 0) return 256;
-    if (g.nx % 128 == 0) return 128;
-    return 0;
+    return g.nx % 128 == 0 ? 128 : 0;
 }
 
 }  // namespace
@@ -375,8 +434,9 @@ cudaError_t launch_step_t3_tma(const Geo& g, const float* phi_in, float* phi_out
     const int xw = width ? width : t3_width(g);
     if (!t3tma_ok(g) || (xw != 128 && xw != 256) || g.nx % xw != 0) return cudaErrorNotSupported;
     if ((((uintptr_t)phi_in | (uintptr_t)v_in) & 15u) != 0) return cudaErrorNotSupported;
-    return xw == 256 ? launch_xw<256>(g, phi_in, phi_out, v_in, v_out, k0, k1, k2, rc, err, st)
-                     : launch_xw<128>(g, phi_in, phi_out, v_in, v_out, k0, k1, k2, rc, err, st);
+    const KickP p0 = kick_packed(k0, rc.deta), p1 = kick_packed(k1, rc.deta), p2 = kick_packed(k2, rc.deta);
+    return xw == 256 ? launch_xw<256>(g, phi_in, phi_out, v_in, v_out, p0, p1, p2, err, st)
+                     : launch_xw<128>(g, phi_in, phi_out, v_in, v_out, p0, p1, p2, err, st);
 }
 
 }  // namespace prs

@@ -78,6 +78,41 @@ __device__ __forceinline__ void update4(float4 c, float left, float right, float
     upk2(fma2(dt, v1, c1), pn.z, pn.w);
 }
 
+// update4 with the constants already packed (KickP): the same operations in the same order,
+// so the same bits.
+__device__ __forceinline__ void update4p(float4 c, float left, float right, float4 yp, float4 ym, float4 zp,
+                                         float4 zm, float4& v, float4& pn, const KickP& k)
+{
+    const f2 kc1{k.c1}, kg{k.g}, kk1{k.k1}, nk2{k.nk2}, dt{k.dt};
+    f2 s0 = pk2(__fadd_rn(c.y, left), __fadd_rn(c.z, c.x));
+    f2 s1 = pk2(__fadd_rn(c.w, c.y), __fadd_rn(right, c.z));
+    s0 = add2(s0, add2(pk2(yp.x, yp.y), pk2(ym.x, ym.y)));
+    s1 = add2(s1, add2(pk2(yp.z, yp.w), pk2(ym.z, ym.w)));
+    s0 = add2(s0, add2(pk2(zp.x, zp.y), pk2(zm.x, zm.y)));
+    s1 = add2(s1, add2(pk2(zp.z, zp.w), pk2(zm.z, zm.w)));
+    const f2 c0 = pk2(c.x, c.y), c1 = pk2(c.z, c.w);
+    const f2 u0 = mul2(c0, fma2(nk2, mul2(c0, c0), kk1));
+    const f2 u1 = mul2(c1, fma2(nk2, mul2(c1, c1), kk1));
+    const f2 v0 = fma2(kc1, pk2(v.x, v.y), fma2(kg, s0, u0));
+    const f2 v1 = fma2(kc1, pk2(v.z, v.w), fma2(kg, s1, u1));
+    upk2(v0, v.x, v.y);
+    upk2(v1, v.z, v.w);
+    upk2(fma2(dt, v0, c0), pn.x, pn.y);
+    upk2(fma2(dt, v1, c1), pn.z, pn.w);
+}
+
+// The scalar kick constants and time step of a packed kick (the low halves), for update1.
+__device__ __forceinline__ KickF kick_scalar(const KickP& k)
+{
+    return KickF{__uint_as_float((unsigned)k.c1), __uint_as_float((unsigned)k.g), __uint_as_float((unsigned)k.k1),
+                 -__uint_as_float((unsigned)k.nk2)};
+}
+
+__device__ __forceinline__ RunConst<float> deta_only(const KickP& k)
+{
+    return RunConst<float>{__uint_as_float((unsigned)k.dt), 0.f, 0.f, 0.f, 0.f, 0.f};
+}
+
 // x-neighbours of a float4 at column `col` of a whole row in shared memory.
 __device__ __forceinline__ void x_halo(const float* row, int col, int nq, int nx, int lane, float4 c, float& left,
                                        float& right)

@@ -98,3 +98,18 @@ def test_default_steps_per_pass(lib):
              ((256, 251, 64), prs.PRS_FP32, 1), ((384, 96, 32), prs.PRS_FP32, 2)]
     for shape, precision, want in cases:
         assert prs.prs_default_tblock(prs.make_params(shape, precision=precision)) == want, shape
+
+
+def test_max_steps_per_pass(lib):
+    """The most steps one pass fuses: three for FP32 3D boxes of the three-step pass (x sides that are
+    multiples of 128, y sides multiples of 8 of at least 16), two for FP32 2D boxes of the two-step
+    pass, one for FP64 and boxes the staged kernels do not take; never below the default."""
+    cases = [((512, 512, 512), prs.PRS_FP32, 3), ((128, 128, 128), prs.PRS_FP32, 3),
+             ((1024, 1024, 1024), prs.PRS_FP32, 3), ((384, 96, 32), prs.PRS_FP32, 3),
+             ((4096, 4096), prs.PRS_FP32, 2), ((2048, 2048), prs.PRS_FP32, 2),
+             ((512, 512, 512), prs.PRS_FP64, 1), ((500, 500, 500), prs.PRS_FP32, 1),
+             ((4096, 4096), prs.PRS_FP64, 1)]
+    for shape, precision, want in cases:
+        p = prs.make_params(shape, precision=precision)
+        assert prs.prs_max_tblock(p) == want, shape
+        assert prs.prs_max_tblock(p) >= prs.prs_default_tblock(p), shape

@@ -63,10 +63,16 @@ def test_interval_calls_split_an_interval(bench):
     """After the fused step + diagnostics, an interval's other steps are one call of whole passes of
     the step kernel (the bracket the roofline times) and a remainder shorter than a pass."""
     for tb in (1, 2):
-        for interval in range(1, 64):
-            pure, tail = bench.interval_calls(interval, tb)
-            assert pure + tail == interval - 1 and pure % tb == 0 and 0 <= tail < tb
-    assert bench.interval_calls(20, 2) == (18, 1) and bench.interval_calls(20, 1) == (19, 0)
+        for tmax in (tb, 3):
+            for interval in range(1, 64):
+                pure, tail, launches = bench.interval_calls(interval, tb, tmax)
+                assert pure + tail == interval - 1 and pure % tb == 0
+                if tb == 2 and tmax == 3 and tail == 3:  # a pair and the odd step as one three-step pass
+                    assert launches == 1 and (interval - 1) % 2 == 1
+                else:
+                    assert 0 <= tail < tb and launches == tail
+    assert bench.interval_calls(20, 2) == (18, 1, 1) and bench.interval_calls(20, 1) == (19, 0, 0)
+    assert bench.interval_calls(20, 2, 3) == (16, 3, 1)
 
 
 def test_kernel_source_hash_and_traffic_record(bench):
