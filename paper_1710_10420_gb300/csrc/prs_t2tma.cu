@@ -58,35 +58,43 @@ static __device__ __noinline__ void drain_planes(uint64_t* bar, int from, int is
     for (int i = from; i <= issued; ++i) mbar_wait(&bar[i & 3], (unsigned)(i >> 2) & 1u, err);
 }
 
-// Per-thread constants of the pass.
-struct Ctx {
+// What the copies of a plane need.  Only thread 0 (and, on the tiles at the ends of y, the
+// last warp) issue copies, so this lives in shared memory rather than in every thread's
+// registers.
+struct Ctx2 {
     const float* phi_in;
     const float* v_in;
-    float* phi_out;
-    float* v_out;
-    float* phi_mid;
-    float* v_mid;
-    float *ring0, *ring1, *ringv;
-    uint64_t* bar;
-    unsigned int* err;
     size_t plane;
-    int nx, ny, nz, x0, y0, z0, zn, nplanes, xl, xr, ywrap;  // ywrap: 0, -1 (top tile), +1 (bottom)
-    int tid, lane;
-    int o0[2], o1[2], e0[2], go[2];  // item offsets: level-0 slot, level-1 slot, x edge, plane
-    bool hal;
-    int hc, hxm, hxp, hv, ho;  // halo lane: offsets in level-0, dphi, level-1 slots
+    int nx, ny, nz, x0, y0, z0, zn, xl, xr, ywrap;  // ywrap: 0, -1 (top tile), +1 (bottom tile)
 };
 
-template <bool MID>
-__device__ __forceinline__ void issue_plane(const Ctx& c, const T2Maps& m, int pl, bool with_v)
+// The CTA's shared memory: mbarriers and the copy context, then the rings.
+struct Smem2 {
+    uint64_t bar[4];
+    Ctx2 c;
+};
+static_assert(sizeof(Smem2) <= 128, "header fits the first 128 bytes");
+
+extern __shared__ __align__(128) unsigned char t2_smem[];
+
+__device__ __forceinline__ Smem2* hdr2() { return reinterpret_cast<Smem2*>(t2_smem); }
+// ring0 (4 phi slots), ring1 (2 level-1 slots), ringv (3 dphi slots), after the header
+__device__ __forceinline__ float* ring0() { return reinterpret_cast<float*>(t2_smem + 128); }
+__device__ __forceinline__ float* ring1() { return ring0() + 4 * kS0; }
+__device__ __forceinline__ float* ringv() { return ring1() + 2 * kS1; }
+
+__device__ __forceinline__ int wrap2(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Stage level-0 plane pl (global z0-2+pl) and, with with_v, the dphi of level-1 plane pl-1
+// into dphi slot vs = (pl-1) mod 3.  Called by every thread; thread 0 issues the tensor copies.
+__device__ __forceinline__ void issue_plane(const T2Maps& m, int tid, int pl, bool with_v, int vs)
 {
-    uint64_t* b = &c.bar[pl & 3];
-    const int zp = pl - 2 + c.z0, zv = pl - 3 + c.z0;  // global planes (before wrapping)
-    const int zg = zp < 0 ? zp + c.nz : (zp >= c.nz ? zp - c.nz : zp);
-    const int zvg = zv < 0 ? zv + c.nz : (zv >= c.nz ? zv - c.nz : zv);
-    float* d0 = c.ring0 + (pl & 3) * kS0;
-    float* dv = c.ringv + ((pl + 2) % 3) * kSV;  // slot of level-1 plane pl-1
-    if (c.tid == 0) {
+    const Ctx2& c = hdr2()->c;
+    uint64_t* b = &hdr2()->bar[pl & 3];
+    if (tid == 0) {
+        const int zg = wrap2(c.z0 - 2 + pl, c.nz), zvg = wrap2(c.z0 - 3 + pl, c.nz);
+        float* d0 = ring0() + (pl & 3) * kS0;
+        float* dv = ringv() + vs * kSV;
         mbar_arrive_expect_tx(b, kBytesPhi + (with_v ? kBytesV : 0u));
         if (c.ywrap == 0) {
             tma_load3(d0, &m.phi12, c.x0, c.y0 - 2, zg, b);
@@ -113,17 +121,19 @@ __device__ __forceinline__ void issue_plane(const Ctx& c, const T2Maps& m, int p
             }
         }
     }
-    if (c.ywrap != 0 && c.tid >= kThreads - 32) {
-        // halo columns row by row (16 bytes each) on the last warp: task t = lane + 32 u;
-        // t < 2 kR0: phi row t/2, side t%2, then the dphi rows
+    if (tid >= kThreads - 32 && c.ywrap != 0) {
+        // the wrap tiles' halo columns row by row (16 bytes each) on the last warp: task
+        // t = lane + 32 u; t < 2 kR0: phi row t/2, side t%2, then the dphi rows
+        const int zg = wrap2(c.z0 - 2 + pl, c.nz), zvg = wrap2(c.z0 - 3 + pl, c.nz);
+        float* d0 = ring0() + (pl & 3) * kS0;
+        float* dv = ringv() + vs * kSV;
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int t = c.lane + 32 * u;
+            const int t = (tid & 31) + 32 * u;
             const bool isv = t >= 2 * kR0;
             if (t >= 2 * (kR0 + kR1) || (isv && !with_v)) continue;
             const int tt = isv ? t - 2 * kR0 : t, r = tt >> 1, side = tt & 1;
-            int y = isv ? c.y0 - 1 + r : c.y0 - 2 + r;
-            y = y < 0 ? y + c.ny : (y >= c.ny ? y - c.ny : y);
+            const int y = wrap2(isv ? c.y0 - 1 + r : c.y0 - 2 + r, c.ny);
             const float* src = (isv ? c.v_in + (size_t)zvg * c.plane : c.phi_in + (size_t)zg * c.plane) +
                                (size_t)y * c.nx + (side ? c.xr : c.xl);
             float* dst = (isv ? dv + (side ? kHRV : kHLV) : d0 + (side ? kHR0 : kHL0)) + 4 * r;
@@ -132,85 +142,99 @@ __device__ __forceinline__ void issue_plane(const Ctx& c, const T2Maps& m, int p
     }
 }
 
-// One plane iteration i of the march.  Level 0 at planes j, j+1 and level 1 at plane k are
-// read from the rings (the stencil reads their x and y neighbours there anyway); only the
-// planes that have left the rings stay in registers: am = level 0 at plane j-1, bm = level
-// 1 at plane k-1, w1 = the level-1 dphi^{n+1/2} at plane k, and the halo lane's level 0 at
-// planes j-1, j (hm, hc).  Returns false when a wait gave up.
-template <bool MID>
-__device__ __forceinline__ bool plane_iter(const Ctx& c, const T2Maps& m, int i, int& issued, const KickF& k0,
-                                           const KickF& k1, const RunConst<float>& rc, float4 (&am)[2],
-                                           float4 (&bm)[2], float4 (&w1)[2], float& hm, float& hc)
+// Per-thread offsets and roles.  Item h of a thread is level-1 float4 q = tid + 320 h: row
+// q / 64 (item 1 sits 5 rows below item 0), column q % 64.
+struct Lane2 {
+    int tid, lane, o0, o1, e0[2];  // item 0's phi-slot and level-1-slot offsets; x-edge offsets
+    bool edge, l2a, l2b, hal;      // l2a, l2b: item 0, 1 runs level 2 (warp-uniform)
+    unsigned hx;                   // halo lane: x neighbours' offsets in the phi slot, hxm | hxp << 16
+    int hc, hv, ho;
+};
+constexpr int kD0 = 5 * kXW, kD1 = 5 * kW1;  // item 1 - item 0 in the phi and level-1 slots
+
+// What a thread carries from plane to plane: level 0 at plane j-1 (am), level 1 at k-1 (bm),
+// the level-1 dphi^{n+1/2} at plane k (w1), and the halo lane's level 0 at j-1 (hm).
+struct Queue2 {
+    float4 am[2], bm[2], w1[2];
+    float hm;
+};
+
+// Plane iteration i with levels 1..LV active (LV = 2 in the steady state, whose body tests
+// no plane ranges; the first four iterations fill the pipeline).  Level 0 at planes j, j+1
+// and level 1 at plane k are read from the rings (the stencil reads their x and y neighbours
+// there anyway).  vs = (i-1) mod 3, the dphi slot of level-1 plane j = i-1.  off: the
+// element offset of item 0's output at level-2 plane k = i-2.  Returns false when a wait
+// gave up.
+template <bool MID, int LV>
+__device__ __forceinline__ bool t2_iter(const T2Maps& m, const Lane2& t, int i, int nplanes, int vs, size_t off,
+                                        int nx5, const KickP& k0, const KickP& k1, Queue2& q, float* phi_out,
+                                        float* v_out, float* phi_mid, float* v_mid, unsigned int* err)
 {
-    const bool ok = mbar_wait(&c.bar[i & 3], (unsigned)(i >> 2) & 1u, c.err);
+    const bool ok = mbar_wait(&hdr2()->bar[i & 3], (unsigned)(i >> 2) & 1u, err);
     if (__syncthreads_or(!ok)) {
-        if (c.tid == 0) drain_planes(c.bar, i, issued, c.err);
+        if (t.tid == 0) drain_planes(hdr2()->bar, i, min(i + 1, nplanes - 1), err);  // planes issued so far
         return false;
     }
-    if (i + 2 < c.nplanes) {
-        issue_plane<MID>(c, m, i + 2, i + 1 >= 1 && i + 1 <= c.zn + 2);
-        issued = i + 2;
-    }
-    const int j = i - 1;  // level-1 plane of this iteration
-    const int k = i - 2;  // level-2 plane of this iteration
-    const float* Ln = c.ring0 + (i & 3) * kS0;        // level-0 plane j+1
-    const float* Lj = c.ring0 + ((i + 3) & 3) * kS0;  // level-0 plane j
-    const float hp = c.hal ? Ln[c.hc] : 0.f;
-    float4 pn[2], w1n[2];  // level 1 at plane j (phi, dphi) of this thread's float4
-    if (j >= 1 && j <= c.zn + 2) {
-        float* L1 = c.ring1 + (j & 1) * kS1;
-        const float* V = c.ringv + (j % 3) * kSV;
+    if (i + 2 < nplanes) issue_plane(m, t.tid, i + 2, true, vs == 0 ? 2 : vs - 1);
+    const int P = i & 1;
+    const float* Ln = ring0() + (i & 3) * kS0;        // level 0 at plane j+1
+    const float* Lj = ring0() + ((i + 3) & 3) * kS0;  // level 0 at plane j
+    float4 pn[2], w1n[2];                             // level 1 at plane j of this thread's items
+    if (LV >= 1) {  // level 1 (step n) at plane j: level 0 at j-1 (am), j, j+1 (ring)
+        float* L1 = ring1() + (P ^ 1) * kS1;
+        const float* V = ringv() + vs * kSV;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const float4 cc = lds4(Lj + c.o0[h]);
-            const float e = Lj[c.e0[h]];  // lane 0: the left neighbour, lane 31: the right one
-            const float su = __shfl_up_sync(0xffffffffu, cc.w, 1), sd = __shfl_down_sync(0xffffffffu, cc.x, 1);
-            const float left = c.lane == 0 ? e : su, right = c.lane == 31 ? e : sd;
-            w1n[h] = lds4(V + c.o0[h] - kXW);  // dphi row = level-1 row
-            update4(cc, left, right, lds4(Lj + c.o0[h] + kXW), lds4(Lj + c.o0[h] - kXW), lds4(Ln + c.o0[h]), am[h],
-                    w1n[h], pn[h], k0, rc, true);
-            *reinterpret_cast<float4*>(L1 + c.o1[h]) = pn[h];
-            am[h] = cc;
+            const int o = t.o0 + h * kD0;
+            const float4 a = lds4(Lj + o);
+            float e = 0.f, left, right;
+            if (t.edge) e = Lj[t.e0[h]];  // lane 0: the left neighbour, lane 31: the right one
+            const float su = __shfl_up_sync(0xffffffffu, a.w, 1), sd = __shfl_down_sync(0xffffffffu, a.x, 1);
+            left = t.lane == 0 ? e : su;
+            right = t.lane == 31 ? e : sd;
+            w1n[h] = lds4(V + o - kXW);  // dphi row = level-1 row
+            update4p(a, left, right, lds4(Lj + o + kXW), lds4(Lj + o - kXW), lds4(Ln + o), q.am[h], w1n[h], pn[h],
+                     k0);
+            *reinterpret_cast<float4*>(L1 + t.o1 + h * kD1) = pn[h];
+            q.am[h] = a;
         }
-        if (c.hal) {
-            float vv = V[c.hv];
-            L1[c.ho] = update1(hc, Lj[c.hxp], Lj[c.hxm], Lj[c.hc + 4], Lj[c.hc - 4], hp, hm, vv, k0, rc, true);
+        if (t.hal) {
+            const float hcen = Lj[t.hc];
+            float vv = V[t.hv];
+            L1[t.ho] = update1(hcen, Lj[t.hx >> 16], Lj[t.hx & 0xffffu], Lj[t.hc + 4], Lj[t.hc - 4], Ln[t.hc], q.hm,
+                               vv, kick_scalar(k0), deta_only(k0), true);
+            q.hm = hcen;
         }
-    } else {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) am[h] = lds4(Lj + c.o0[h]);
     }
-    hm = hc;
-    hc = hp;
-    if (k >= 2 && k <= c.zn + 1) {
-        const float* L1 = c.ring1 + (k & 1) * kS1;
-        const size_t zo = (size_t)(c.z0 - 2 + k) * c.plane;
+    if (LV >= 2) {  // level 2 (step n+1) at plane k: level 1 at k-1 (bm), k (ring), k+1 (pn)
+        const float* L1 = ring1() + P * kS1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if (h == 0 ? c.tid < 64 : c.tid >= 256) continue;  // the level-1 halo rows 0, 9 (warp-uniform)
-            const float4 cc = lds4(L1 + c.o1[h]);
-            const float e = L1[c.o1[h] + (c.lane == 0 ? -1 : 4)];
-            const float su = __shfl_up_sync(0xffffffffu, cc.w, 1), sd = __shfl_down_sync(0xffffffffu, cc.x, 1);
-            const float left = c.lane == 0 ? e : su, right = c.lane == 31 ? e : sd;
-            float4 vv = w1[h];
+            if (!(h == 0 ? t.l2a : t.l2b)) continue;  // the level-1 halo rows 0, 9
+            const int o = t.o1 + h * kD1;
+            const float4 b = lds4(L1 + o);
+            float e = 0.f, left, right;
+            if (t.edge) e = L1[o + (t.lane == 0 ? -1 : 4)];
+            const float su = __shfl_up_sync(0xffffffffu, b.w, 1), sd = __shfl_down_sync(0xffffffffu, b.x, 1);
+            left = t.lane == 0 ? e : su;
+            right = t.lane == 31 ? e : sd;
+            float4 vv = q.w1[h];
+            const size_t go = off + (size_t)(h * nx5);
             if (MID) {
-                stg4(c.phi_mid + zo + c.go[h], cc);
-                stg4(c.v_mid + zo + c.go[h], vv);
+                stg4(phi_mid + go, b);
+                stg4(v_mid + go, vv);
             }
             float4 out;
-            update4(cc, left, right, lds4(L1 + c.o1[h] + kW1), lds4(L1 + c.o1[h] - kW1), pn[h], bm[h], vv, out, k1, rc,
-                    true);
-            stg4(c.phi_out + zo + c.go[h], out);
-            stg4(c.v_out + zo + c.go[h], vv);
-            bm[h] = cc;
+            update4p(b, left, right, lds4(L1 + o + kW1), lds4(L1 + o - kW1), pn[h], q.bm[h], vv, out, k1);
+            stg4(phi_out + go, out);
+            stg4(v_out + go, vv);
+            q.bm[h] = b;
         }
-    } else if (k == 1) {  // level 1 at plane 1, the first level-2 plane's z neighbour below
-        const float* L1 = c.ring1 + kS1;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) bm[h] = lds4(L1 + c.o1[h]);
     }
+    if (LV >= 1) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) w1[h] = w1n[h];
+        for (int h = 0; h < 2; ++h) q.w1[h] = w1n[h];
+    }
     return true;
 }
 
@@ -218,84 +242,79 @@ template <bool MID>
 __global__ void __launch_bounds__(kThreads, 2)
     k_step3d_t2tma(const __grid_constant__ T2Maps maps, const float* __restrict__ phi_in, float* __restrict__ phi_out,
                    const float* __restrict__ v_in, float* __restrict__ v_out, float* __restrict__ phi_mid,
-                   float* __restrict__ v_mid, int nx, int ny, int nz, int cz, KickF k0, KickF k1, RunConst<float> rc,
-                   unsigned int* err)
+                   float* __restrict__ v_mid, int nx, int ny, int nz, int cz, KickP k0, KickP k1, unsigned int* err)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Ctx c;
-    c.bar = reinterpret_cast<uint64_t*>(smem_raw);
-    c.ring0 = reinterpret_cast<float*>(smem_raw + 128);
-    c.ring1 = c.ring0 + 4 * kS0;
-    c.ringv = c.ring1 + 2 * kS1;
-    c.phi_in = phi_in;
-    c.v_in = v_in;
-    c.phi_out = phi_out;
-    c.v_out = v_out;
-    c.phi_mid = phi_mid;
-    c.v_mid = v_mid;
-    c.err = err;
-    c.nx = nx;
-    c.ny = ny;
-    c.nz = nz;
-    c.plane = (size_t)nx * ny;
-    c.tid = threadIdx.x;
-    c.lane = c.tid & 31;
     const int nxt = nx / kXW, ytiles = ny / kTY;
-    c.x0 = (blockIdx.x % nxt) * kXW;
-    c.y0 = (blockIdx.x / nxt % ytiles) * kTY;
-    c.z0 = blockIdx.x / nxt / ytiles * cz;
-    c.zn = min(cz, nz - c.z0);
-    c.nplanes = c.zn + 4;  // level-0 local planes 0..zn+3 = global z0-2 .. z0+zn+1
-    c.xl = c.x0 >= 4 ? c.x0 - 4 : c.x0 - 4 + nx;
-    c.xr = c.x0 + kXW < nx ? c.x0 + kXW : 0;
-    c.ywrap = c.y0 == 0 ? -1 : (c.y0 + kTY == ny ? 1 : 0);
+    const int x0 = (blockIdx.x % nxt) * kXW, y0 = (blockIdx.x / nxt % ytiles) * kTY, z0 = blockIdx.x / nxt / ytiles * cz;
+    const int zn = min(cz, nz - z0);
+    const int nplanes = zn + 4;  // level-0 local planes 0..zn+3 = global z0-2 .. z0+zn+1
+    const size_t plane = (size_t)nx * ny;
 
-    // this thread's level-1 float4: item h is q = tid + 320 h, level-1 row q / 64, column q % 64
+    Lane2 t;
+    t.tid = threadIdx.x;
+    t.lane = t.tid & 31;
+    const int row = t.tid >> 6, col = t.tid & 63;  // item 0; item 1 is row + 5
+    t.o0 = (row + 1) * kXW + 4 * col;  // phi slot (phi row row+1); dphi slot at o0 - kXW
+    t.o1 = row * kW1 + 4 + 4 * col;    // level-1 slot
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int q = c.tid + kThreads * h, row = q >> 6, col = q & 63;
-        c.o0[h] = (row + 1) * kXW + 4 * col;      // level-0 slot (level-0 row row+1)
-        c.o1[h] = row * kW1 + 4 + 4 * col;        // level-1 slot
         // x neighbour beyond the warp's 32 float4: lane 0 reads the left one, lane 31 the right
-        const int el = col == 0 ? kHL0 + (row + 1) * 4 + 3 : c.o0[h] - 1;
-        const int er = col == 63 ? kHR0 + (row + 1) * 4 : c.o0[h] + 4;
-        c.e0[h] = c.lane == 0 ? el : er;
-        c.go[h] = (c.y0 - 1 + row) * nx + c.x0 + 4 * col;
+        const int r = row + 5 * h, o = t.o0 + h * kD0;
+        t.e0[h] = t.lane == 0 ? (col == 0 ? kHL0 + (r + 1) * 4 + 3 : o - 1) : (col == 63 ? kHR0 + (r + 1) * 4 : o + 4);
     }
+    t.edge = t.lane == 0 || t.lane == 31;
+    t.l2a = t.tid >= 64;   // item 0 on level-1 rows 1..4
+    t.l2b = t.tid < 256;   // item 1 on level-1 rows 5..8
     // halo lanes: thread t < 2 kR1 computes level 1 at row t/2, column x0-1 (t even) or x0+256
-    c.hal = c.tid < 2 * kR1;
-    {
-        const int r = c.tid >> 1;
-        if ((c.tid & 1) == 0) {
-            c.hc = kHL0 + (r + 1) * 4 + 3;
-            c.hxm = c.hc - 1;
-            c.hxp = (r + 1) * kXW;
-            c.hv = kHLV + r * 4 + 3;
-            c.ho = r * kW1 + 3;
+    t.hal = t.tid < 2 * kR1;
+    t.hc = 4, t.hx = 0, t.hv = 0, t.ho = 0;
+    if (t.hal) {
+        const int r = t.tid >> 1;
+        if ((t.tid & 1) == 0) {
+            t.hc = kHL0 + (r + 1) * 4 + 3;
+            t.hx = (unsigned)(t.hc - 1) | (unsigned)((r + 1) * kXW) << 16;
+            t.hv = kHLV + r * 4 + 3;
+            t.ho = r * kW1 + 3;
         } else {
-            c.hc = kHR0 + (r + 1) * 4;
-            c.hxm = (r + 1) * kXW + kXW - 1;
-            c.hxp = c.hc + 1;
-            c.hv = kHRV + r * 4;
-            c.ho = r * kW1 + kXW + 4;
+            t.hc = kHR0 + (r + 1) * 4;
+            t.hx = (unsigned)((r + 1) * kXW + kXW - 1) | (unsigned)(t.hc + 1) << 16;
+            t.hv = kHRV + r * 4;
+            t.ho = r * kW1 + kXW + 4;
         }
-        if (!c.hal) c.hc = 4, c.hxm = c.hxp = c.hv = c.ho = 0;
     }
-    if (c.tid == 0) {
+    if (t.tid == 0) {
+        Smem2* sm = hdr2();
+        sm->c = Ctx2{phi_in, v_in, plane, nx, ny, nz, x0, y0, z0, zn, x0 >= 4 ? x0 - 4 : x0 - 4 + nx,
+                     x0 + kXW < nx ? x0 + kXW : 0, y0 == 0 ? -1 : (y0 + kTY == ny ? 1 : 0)};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&c.bar[i], 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&sm->bar[i], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    issue_plane<MID>(c, maps, 0, false);
-    issue_plane<MID>(c, maps, 1, false);
-    int issued = 1;
+    issue_plane(maps, t.tid, 0, false, 0);
+    issue_plane(maps, t.tid, 1, false, 0);
 
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 am[2] = {z4, z4}, bm[2] = {z4, z4}, w1[2] = {z4, z4};
-    float hm = 0.f, hc = 0.f;
-    for (int i = 0; i < c.nplanes; ++i)
-        if (!plane_iter<MID>(c, maps, i, issued, k0, k1, rc, am, bm, w1, hm, hc)) return;
+    Queue2 q;
+    const int nx5 = 5 * nx;
+    size_t off = (size_t)z0 * plane + (size_t)(y0 - 1 + row) * nx + x0 + 4 * col;  // level-2 plane 2 = z0
+    // pipeline fill: iterations 0, 1 only stage planes; level 1 starts at 2, level 2 at 4; the
+    // queues' first planes are read where they are first needed
+    if (!t2_iter<MID, 0>(maps, t, 0, nplanes, 2, off, nx5, k0, k1, q, phi_out, v_out, phi_mid, v_mid, err)) return;
+    if (!t2_iter<MID, 0>(maps, t, 1, nplanes, 0, off, nx5, k0, k1, q, phi_out, v_out, phi_mid, v_mid, err)) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) q.am[h] = lds4(ring0() + t.o0 + h * kD0);  // level 0 at plane 0 (slot 0)
+    if (t.hal) q.hm = ring0()[t.hc];
+    if (!t2_iter<MID, 1>(maps, t, 2, nplanes, 1, off, nx5, k0, k1, q, phi_out, v_out, phi_mid, v_mid, err)) return;
+    if (!t2_iter<MID, 1>(maps, t, 3, nplanes, 2, off, nx5, k0, k1, q, phi_out, v_out, phi_mid, v_mid, err)) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) q.bm[h] = lds4(ring1() + kS1 + t.o1 + h * kD1);  // level 1 at plane 1 (slot 1)
+    int vs = 0;  // (i-1) mod 3 at i = 4
+    for (int i = 4; i < nplanes; ++i) {
+        if (!t2_iter<MID, 2>(maps, t, i, nplanes, vs, off, nx5, k0, k1, q, phi_out, v_out, phi_mid, v_mid, err))
+            return;
+        off += plane;
+        vs = vs == 2 ? 0 : vs + 1;
+    }
 }
 
 }  // namespace
@@ -353,6 +372,7 @@ cudaError_t launch_step_t2_tma(const Geo& g, const float* phi_in, float* phi_out
         !tmap_encode(f, &m.v1, v_in, g, kXW, 1) || !tmap_encode(f, &m.vh, v_in, g, 4, kR1))
         return cudaErrorNotSupported;
     const bool mid = phi_mid != nullptr;
+    const KickP p0 = kick_packed(k0, rc.deta), p1 = kick_packed(k1, rc.deta);
     const void* fn = mid ? (const void*)k_step3d_t2tma<true> : (const void*)k_step3d_t2tma<false>;
     static std::atomic<unsigned long long> attr[2];
     cudaError_t e = smem_limit_once(attr[mid ? 1 : 0], fn, (int)kSmem);
@@ -380,10 +400,10 @@ cudaError_t launch_step_t2_tma(const Geo& g, const float* phi_in, float* phi_out
     if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
     if (mid)
         k_step3d_t2tma<true><<<(unsigned)blocks, kThreads, kSmem, st>>>(m, phi_in, phi_out, v_in, v_out, phi_mid, v_mid,
-                                                                       g.nx, g.ny, g.nz, cz, k0, k1, rc, err);
+                                                                       g.nx, g.ny, g.nz, cz, p0, p1, err);
     else
         k_step3d_t2tma<false><<<(unsigned)blocks, kThreads, kSmem, st>>>(m, phi_in, phi_out, v_in, v_out, nullptr,
-                                                                        nullptr, g.nx, g.ny, g.nz, cz, k0, k1, rc, err);
+                                                                        nullptr, g.nx, g.ny, g.nz, cz, p0, p1, err);
     return cudaGetLastError();
 }
 
