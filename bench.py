@@ -266,7 +266,13 @@ def peaks():
 # by steps per pass
 STEP_KERNEL_SOURCES = {1: ("prs_fast.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_reduce.cuh",
                            "prs_f32x2.cuh"),
-                       2: ("prs_t2tma.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_f32x2.cuh")}
+                       2: ("prs_t2tma.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_f32x2.cuh",
+                           "prs_tmap.h"),
+                       3: ("prs_t3tma.cu", "prs_tile.cuh", "prs_ptx.cuh", "prs_internal.h", "prs_f32x2.cuh",
+                           "prs_tmap.h")}
+STEP_KERNELS_3D = {1: "k_step3d_f32, one leapfrog step per pass",
+                   2: "k_step3d_t2tma, two leapfrog steps per pass",
+                   3: "k_step3d_t3tma, three leapfrog steps per pass"}
 
 
 def kernel_sources_sha(names=STEP_KERNEL_SOURCES[2]) -> str:
@@ -284,9 +290,12 @@ def traffic_record(workload: str, tblock: int):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            rec = json.load(f).get(workload)
+            recs = json.load(f)
     except (OSError, ValueError):
         return None
+    rec = recs.get(workload)
+    if not rec or rec.get("tblock", 1) != tblock:
+        rec = recs.get(f"{workload}/tblock{tblock}")
     if not rec or rec.get("tblock", 1) != tblock:
         return None
     if rec.get("sources_sha") != kernel_sources_sha(tuple(rec.get("sources", STEP_KERNEL_SOURCES[tblock]))):
@@ -407,9 +416,7 @@ def run_gpu(args, world, rank, local):
     rec = traffic_record(args.workload, tb)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (rec["dram_bytes_per_launch"] if rec else None),
-                "kernel": ("k_step3d_t2tma, two leapfrog steps per pass" if tb == 2 else
-                           "k_step3d_f32, one leapfrog step per pass") if len(shape) == 3 else
-                          f"2D step kernel, {tb} leapfrog step(s) per pass",
+                "kernel": STEP_KERNELS_3D[tb] if len(shape) == 3 else f"2D step kernel, {tb} leapfrog step(s) per pass",
                 "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_site_update": alg_bytes / (sites * tb),
                 "launches_timed": len(events) * (pure_launches or step_launches),
                 "note": "achieved = the pass's algorithmic bytes (16 B per site, read and write of phi and dphi) "
