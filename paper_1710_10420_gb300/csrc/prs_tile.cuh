@@ -390,6 +390,12 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const KickF& k, const Ru
         row[j] = q / nq;
         col[j] = q - row[j] * nq;
     }
+    // With whole 1024-wide rows and four items, a thread's items are the four rows of its
+    // column: item j's +y and -y rows are items j+1 and j-1, and a plane's -z masks are the
+    // previous plane's centre masks, whose own centre masks were its +z masks.  So a plane
+    // computes 6 sign masks per thread (the +z plane's four and the two halo rows) instead of 20.
+    constexpr bool kReuse = MEAS && NX == 1024 && ITEMS == 4;
+    unsigned cmask[ITEMS], zmask[ITEMS];  // kReuse: this plane's and the previous plane's masks
     float4 vc[ITEMS];
     {
         const float* vb = T.v_in + (size_t)z0 * plane + (size_t)y0 * nx;
@@ -422,6 +428,15 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const KickF& k, const Ru
         const float* pp = ring + ((zi + 2) & 3) * tile + nx;
         float* po = T.phi_out + (size_t)z * plane + (size_t)y0 * nx;
         float* vo = T.v_out + (size_t)z * plane + (size_t)y0 * nx;
+        if (kReuse && zi == 0) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const int off = row[j] * nx + 4 * col[j];
+                cmask[j] = negmask4(lds4(pc + off));
+                zmask[j] = negmask4(lds4(pm + off));
+            }
+        }
+        unsigned nmask[ITEMS];  // kReuse: the +z plane's masks, the next plane's centre masks
         int qn = 0;  // this warp's queued links (MEAS)
         // one queued link: item j's row and first column are the same in all lanes of
         // the warp (its 32 float4 are consecutive in one row)
@@ -445,11 +460,25 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const KickF& k, const Ru
             float left, right;
             x_halo(pc + r * nx, col[j], nq, nx, lane, c, left, right);
             if (MEAS) {
-                const unsigned sc = negmask4(c);
+                unsigned sc, syp, sym, szp, szm;
+                if (kReuse) {
+                    sc = cmask[j];
+                    sym = j > 0 ? cmask[j > 0 ? j - 1 : 0] : negmask4(ym);
+                    syp = j < ITEMS - 1 ? cmask[j < ITEMS - 1 ? j + 1 : 0] : negmask4(yp);
+                    szm = zmask[j];
+                    szp = negmask4(zp);
+                    nmask[j] = szp;
+                } else {
+                    sc = negmask4(c);
+                    sym = negmask4(ym);
+                    syp = negmask4(yp);
+                    szm = negmask4(zm);
+                    szp = negmask4(zp);
+                }
                 const unsigned sxp = (sc >> 1) | (right < 0.0f ? 8u : 0u);
                 const unsigned sxm = ((sc << 1) & 15u) | (left < 0.0f ? 1u : 0u);
-                const unsigned lx = sc ^ sxp, ly = sc ^ negmask4(yp), lz = sc ^ negmask4(zp);
-                const unsigned wall = lx | ly | lz | (sc ^ sxm) | (sc ^ negmask4(ym)) | (sc ^ negmask4(zm));
+                const unsigned lx = sc ^ sxp, ly = sc ^ syp, lz = sc ^ szp;
+                const unsigned wall = lx | ly | lz | (sc ^ sxm) | (sc ^ sym) | (sc ^ szm);
                 wall_sites4(a, wall, c, vc[j], rc);
                 // bit 4d+e: the link from site e along axis d crosses
                 const unsigned lmask = lx | (ly << 4) | (lz << 8);
@@ -467,6 +496,10 @@ __device__ __forceinline__ bool tile3d(const Tile3D& T, const KickF& k, const Ru
         if (MEAS) {
             qn = run_link_rounds(wq, qn, true, lane, link3);
             a.fold(rscale);
+        }
+        if (kReuse) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) zmask[j] = cmask[j], cmask[j] = nmask[j];
         }
         if (zi + 1 < zn) {
 #pragma unroll

@@ -102,3 +102,40 @@ def test_stability_checked_at_both_ends():
     assert e.value.status == prs.PRS_EINVAL
     assert sim.get_state()[2] == 10
     sim.close()
+
+
+@pytest.mark.parametrize("owned", [True, False])
+def test_default_passes_take_a_triple_for_odd_counts(owned):
+    """With the library's choice of steps per pass (two here), an odd step count on a box of the
+    three-step pass runs one three-step pass in place of a pair and a single step: library-owned
+    buffers keep every multi-step pass (dphi alternates between the two buffers), bound buffers keep
+    dphi at home after every call; the field follows the oracle either way."""
+    import torch
+
+    shape = (384, 16, 24)
+    calls = (19, 3, 1, 5, 2, 7)
+    p = prs.make_params(shape, seed=6)
+    assert prs.prs_default_tblock(p) == 2 and prs.prs_max_tblock(p) == 3
+    fshape = tuple(reversed(shape))
+    if owned:
+        h = prs.prs_create(p)
+        prs.prs_init(h)
+        for k in calls:
+            prs.prs_step(h, k)
+        phi = np.empty(fshape, np.float32)
+        v = np.empty(fshape, np.float32)
+        n = prs.prs_get_state(h, phi, v)
+        prs.prs_destroy(h)
+    else:
+        sim = prs.Sim(shape, seed=6)
+        sim.init()
+        home = sim._bufs[2].data_ptr()
+        for k in calls:
+            sim.step(k)
+            assert prs.prs_device_state(sim.handle)[1] == home
+        phi, v, n = sim.get_state()
+        sim.close()
+    op = oracle.Params(shape)
+    ophi, ov = oracle.step(op, *oracle.init_random(op, 6), sum(calls))
+    assert n == sum(calls) and _rel(phi, ophi) <= 1e-5 and _rel(v, ov) <= 1e-5
+    torch.cuda.synchronize()
