@@ -669,15 +669,15 @@ def run_2d_figure(prs, stream, dev, interval: int) -> dict:
     ms = a.elapsed_time(z)
     sim.close()
     peak, kind = peaks()
-    per_step = step_ms / (k * (interval - 1))  # the plain steps of an interval, in one- or two-step passes
+    per_step = step_ms / (k * (interval - 1))  # the plain steps of an interval, in multi-step passes
     tb = lib_default_tblock(prs, shape)
     return {"workload": "2D 4096^2 FP32 PRS step (5-point), radiation era, 20 steps + FP64 wall diagnostics "
                         "(state 192 MB: L2-sized, not flushed)",
             "value": sites * interval * k / (ms / 1e3), "unit": "site-updates/s", "ms_per_step": ms / k,
             "fused_steps_per_pass": tb, "ms_per_leapfrog_step": per_step,
             "effective_frac_of_copy_bw": 16.0 * sites / (per_step / 1e3) / 1e9 / peak,
-            "note": "effective = 16 B per site-update over the time per step; with two steps per pass the "
-                    "DRAM traffic is half of that"}
+            "note": "effective = 16 B per site-update over the time per step; with two or three steps per "
+                    "pass the DRAM traffic is a half or a third of that"}
 
 
 def run_precision_figure(prs, stream, dev) -> dict:

@@ -105,15 +105,16 @@ typedef struct {
     uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
     uint32_t flags;    /* PRS_REPRO | PRS_FP32_CR | PRS_DEBUG, or 0                 */
     int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (2 for
-                          FP32 3D boxes whose two-step tiles get at least 4 rows of y
-                          and FP32 2D boxes of at least 2^24 sites, else 1; see
-                          prs_default_tblock); 2 = two-step passes for FP32 boxes with
+                          FP32 3D boxes whose two-step tiles get at least 4 rows of y;
+                          for FP32 2D boxes of at least 2^24 sites 3 on rows wider than
+                          2048, else 2; else 1; see prs_default_tblock); 2 = two-step passes for FP32 boxes with
                           an x side that is a multiple of 128 (3D; z side >= 3) or a
                           multiple of 128 up to 4096 (2D), else 1; 3 = three-step
                           passes for FP32 3D boxes with an x side that is a multiple
                           of 128, a y side that is a multiple of 8 (at least 16) and
-                          a z side >= 3, else as 2; at most 8 (values above the
-                          box's limit act as that limit)                            */
+                          a z side >= 3, and for FP32 2D boxes with an x side that is
+                          a multiple of 128 up to 4096, else as 2; at most 8 (values
+                          above the box's limit act as that limit)                  */
 } prs_params;
 
 /* One output record of the wall diagnostics (Eq. 7, Eq. 8). */
@@ -344,8 +345,8 @@ int prs_coefficients(const prs_params* params, int64_t n, double out[5]);
 int prs_default_tblock(const prs_params* params);
 
 /* The most leapfrog steps one pass over HBM can fuse for these parameters (>= 1; a
- * params->tblock above it acts as it): 3 for FP32 3D boxes the three-step pass takes, 2
- * for the other boxes of the two-step passes, else 1; or a negative status for invalid
+ * params->tblock above it acts as it): 3 for FP32 2D and 3D boxes the three-step passes
+ * take, 2 for the other boxes of the two-step passes, else 1; or a negative status for invalid
  * parameters.  Follows the fusion of Eqs. 3-5 over several steps, which the paper does
  * not do (it launches one kernel per equation and step, Sec. III). */
 int prs_max_tblock(const prs_params* params);

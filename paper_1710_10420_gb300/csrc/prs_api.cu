@@ -498,9 +498,9 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
         cudaError_t e;
         if (t == 3) {
             step_coefficients(s->p, n + 2, c);
-            e = launch_step_t3_tma(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
-                                   (const float*)vbuf[vi], (float*)vbuf[1 - vi], kick_f32(a, s->rc),
-                                   kick_f32(b, s->rc), kick_f32(c, s->rc), rcf, err, s->stream);
+            e = launch_step_t3(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
+                               (const float*)vbuf[vi], (float*)vbuf[1 - vi], kick_f32(a, s->rc), kick_f32(b, s->rc),
+                               kick_f32(c, s->rc), rcf, err, s->stream);
             if (e == cudaErrorNotSupported) {  // no tensor-map encoder: a pair, then a single step in place
                 e = launch_step_t2(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
                                    (const float*)vbuf[vi], (float*)vbuf[1 - vi], kick_f32(a, s->rc),

@@ -165,6 +165,16 @@ cudaError_t launch_step_t3_tma(const Geo& g, const float* phi_in, float* phi_out
                                KickF k0, KickF k1, KickF k2, RunConst<float> rc, unsigned int* err, cudaStream_t st,
                                int width = 0);
 
+// Three fused leapfrog steps per pass on FP32 2D boxes (prs_t3_2d.cu): x sides that are
+// multiples of 128 up to 4096; dphi out of place.
+bool t3_2d_ok(const Geo& g);
+cudaError_t launch_step_t3_2d(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
+                              KickF k0, KickF k1, KickF k2, RunConst<float> rc, unsigned int* err, cudaStream_t st);
+
+// One three-step pass on whichever kernel takes the box (3D tensor-copy tiles or 2D rows).
+cudaError_t launch_step_t3(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
+                           KickF k0, KickF k1, KickF k2, RunConst<float> rc, unsigned int* err, cudaStream_t st);
+
 // Store a message for prs_last_error() on this thread.
 void record_error(const char* msg);
 

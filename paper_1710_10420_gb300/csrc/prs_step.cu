@@ -15,28 +15,39 @@ KickF kick_f32(const double coef[3], const double run_const[6])
     return KickF{(float)coef[0], (float)g, (float)(h - run_const[3] * g), (float)(h * run_const[2])};
 }
 
-// Steps one pass may fuse (params.tblock above this is clamped): three on the FP32 3D boxes
-// the three-step pass takes, two on the other boxes of the two-step passes.
+// Steps one pass may fuse (params.tblock above this is clamped): three on the FP32 boxes the
+// three-step passes take, two on the other boxes of the two-step passes.
 int max_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)repro;
     if (!tblock_ok(g, precision)) return 1;
-    return t3tma_ok(g) ? 3 : 2;
+    return (g.dims == 3 ? t3tma_ok(g) : t3_2d_ok(g)) ? 3 : 2;
+}
+
+cudaError_t launch_step_t3(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
+                           KickF k0, KickF k1, KickF k2, RunConst<float> rc, unsigned int* err, cudaStream_t st)
+{
+    if (g.dims == 2) return launch_step_t3_2d(g, phi_in, phi_out, v_in, v_out, k0, k1, k2, rc, err, st);
+    return launch_step_t3_tma(g, phi_in, phi_out, v_in, v_out, k0, k1, k2, rc, err, st);
 }
 
 // The library's default number of steps per pass.  FP32 3D: two wherever the two-step
 // pass gets tiles of at least 4 rows (fewer rows make level 1 recompute more than it
 // saves) — per step against one step per pass, measured 13.6 against 22.7 us at 128^3,
 // 38.2 against 48.2 us at 256^3, 0.230 against 0.323 ms at 512^3 and 1.67 against 2.53 ms
-// at 1024^3.  FP32 2D: two once the state (three fields) outgrows L2 — rows are
-// whole, so level 1 recomputes only the two rows outside each chunk (4096^2: 26 us
-// against 48 us per step); an L2-resident state (2048^2) steps about as fast one step at a
-// time (10.6 against 10.4 us).  FP64 and other boxes: one.
+// at 1024^3.  FP32 2D, once the state (three fields) outgrows L2: three on rows wider than
+// 2048 (every thread of the 512-thread row kernels holds two float4; 4096^2: 22.6 us per step
+// against 25.7 two at a time and 47.0 one at a time), else two — rows are whole, so the levels
+// recompute only the rows outside each chunk; an L2-resident state (2048^2) steps about as
+// fast one step at a time (10.3 against 11.0 and 10.3 us).  FP64 and other boxes: one.
 int default_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)repro;
     if (precision != PRS_FP32 || !tblock_ok(g, precision)) return 1;
-    if (g.dims == 2) return g.S >= (int64_t)1 << 24 ? 2 : 1;
+    if (g.dims == 2) {
+        if (g.S < (int64_t)1 << 24) return 1;
+        return t3_2d_ok(g) && g.nx > 2048 ? 3 : 2;
+    }
     return tblock3_rows(g) >= 4 ? 2 : 1;
 }
 

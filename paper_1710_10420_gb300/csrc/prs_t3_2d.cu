@@ -1,0 +1,226 @@
+// prs_t3_2d.cu -- three leapfrog steps (Eqs. 3-5) per pass over HBM, FP32 2D, whole rows.
+//
+// A CTA owns the rows [y0, y0+yn) of a chunk (one chunk per SM) and marches along y, one row
+// per iteration, through three levels on whole rows (x neighbours by warp shuffle, the
+// periodic wrap by lanes 0/31):
+//   level 1 (step n)   on rows y0-2 .. y0+yn+1, from level-0 rows y0-3 .. y0+yn+2 that the
+//                       TMA engine stages into a ring, three rows ahead;
+//   level 2 (step n+1) on rows y0-1 .. y0+yn, from the level-1 ring;
+//   level 3 (step n+2) on the chunk's rows, from the level-2 ring, to HBM.
+// Iteration i runs level 1 on local row i-1, level 2 on row i-3 and level 3 on row i-5: each
+// level reads only rows that the level before it wrote in earlier iterations, so one barrier
+// per row orders everything.  A thread owns the same columns of every row, so the dphi that
+// level 1 hands to level 2 (and level 2 to level 3) stays in its registers, two rows deep.
+// Only the rows outside the chunk (four at level 1, two at level 2) are computed twice.
+// dphi enters those rows from the neighbouring chunks, so it is read from one buffer and
+// written to another.  At one SM per chunk the two-step pass streams its rows at about the
+// SM's share of the copy bandwidth, so the third level's gain is the bytes it saves.
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "prs_internal.h"
+#include "prs_ptx.cuh"
+#include "prs_tile.cuh"
+
+namespace prs {
+
+namespace {
+
+constexpr int kT3Threads = 512;
+constexpr int kAhead = 3;            // level-0 rows in flight
+constexpr int kSlots0 = 3 + kAhead;  // level-0 ring rows: three read, kAhead in flight
+constexpr int kSlots1 = 4;           // level-1 ring rows: three read by level 2, one written
+constexpr int kSlots2 = 4;           // level-2 ring rows: three read by level 3, one written
+
+size_t smem2d_t3(int nx) { return 128 + (size_t)(kSlots0 + kSlots1 + kSlots2) * nx * sizeof(float); }
+
+static __device__ __noinline__ void drain_rows3(uint64_t* bar, int from, int issued, unsigned int* err)
+{
+    for (int i = from; i <= issued; ++i) mbar_wait(&bar[i % kSlots0], (unsigned)(i / kSlots0) & 1u, err);
+}
+
+__device__ __forceinline__ int wrap_row(int y, int ny)
+{
+    while (y < 0) y += ny;
+    while (y >= ny) y -= ny;
+    return y;
+}
+
+// One level's update of a row from its ring rows below (m), at (c) and above (p): reads x
+// neighbours by shuffle; vv is this thread's dphi (updated in place), pn the new phi.
+template <int ITEMS>
+__device__ __forceinline__ void row_update(const float* m, const float* c, const float* p, const int (&col)[ITEMS],
+                                           const bool (&on)[ITEMS], int nq, int nx, int lane, float4 (&vv)[ITEMS],
+                                           float4 (&pn)[ITEMS], const KickP& k)
+{
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        if (!on[j]) continue;
+        const float4 cc = lds4(c + 4 * col[j]);
+        float left, right;
+        x_halo(c, col[j], nq, nx, lane, cc, left, right);
+        const float4 ym = lds4(m + 4 * col[j]);
+        update4p<false>(cc, left, right, lds4(p + 4 * col[j]), ym, ym, ym, vv[j], pn[j], k);
+    }
+}
+
+// NX > 0: the row width as a compile-time constant (the 4096-wide production box).
+template <int ITEMS, int NX>
+__global__ void __launch_bounds__(kT3Threads, 1)
+    k_step2d_t3(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
+                float* __restrict__ v_out, int nx_, int ny, int cy, KickP k0, KickP k1, KickP k2, unsigned int* err)
+{
+    const int nx = NX > 0 ? NX : nx_;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* ring0 = reinterpret_cast<float*>(smem_raw + 128);
+    float* ring1 = ring0 + kSlots0 * nx;
+    float* ring2 = ring1 + kSlots1 * nx;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int y0 = blockIdx.x * cy;
+    const int yn = min(cy, ny - y0);
+    const int nq = nx >> 2;
+    const int nload = yn + 6;  // level-0 local rows 0 .. yn+5 = global y0-3 .. y0+yn+2
+
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < kSlots0; ++i) mbar_init(&bar[i], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const unsigned rowb = (unsigned)nx * 4u;
+    auto issue = [&](int i) {  // level-0 local row i into slot i mod kSlots0
+        uint64_t* b = &bar[i % kSlots0];
+        mbar_arrive_expect_tx(b, rowb);
+        bulk_g2s(ring0 + (i % kSlots0) * nx, phi_in + (size_t)wrap_row(y0 - 3 + i, ny) * nx, rowb, b);
+    };
+    // row r may be staged once row r - kSlots0, last read by level 1 at iteration r - kSlots0 + 2,
+    // is done with: at iteration r - kAhead
+    int issued = -1;
+    if (tid == 0)
+        for (int i = 0; i < kAhead && i < nload; ++i) issue(i), issued = i;
+
+    int col[ITEMS];
+    bool on[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int q = tid + kT3Threads * j;
+        on[j] = q < nq;
+        col[j] = on[j] ? q : 0;
+    }
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // vn: dphi^{n-1/2} of level-1 row j+1, loaded an iteration ahead; w1a/w1b: level-1 dphi
+    // handed down one and two iterations ago; w2a/w2b: the same for level 2
+    float4 vn[ITEMS], w1a[ITEMS], w1b[ITEMS], w2a[ITEMS], w2b[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) vn[j] = w1a[j] = w1b[j] = w2a[j] = w2b[j] = z4;
+    auto load_v = [&](int jl) {  // dphi of level-1 local row jl (global y0-3+jl)
+        if (jl < 1 || jl > yn + 4) return;
+        const float* vp = v_in + (size_t)wrap_row(y0 - 3 + jl, ny) * nx;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j)
+            if (on[j]) vn[j] = ldg_stream4(vp + 4 * col[j]);
+    };
+    load_v(1);
+
+    const int iters = yn + 8;  // level 3 reaches local row yn+2 at iteration yn+7
+    for (int i = 0; i < iters; ++i) {
+        bool ok = true;
+        if (i < nload) ok = mbar_wait(&bar[i % kSlots0], (unsigned)(i / kSlots0) & 1u, err);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) drain_rows3(bar, i, issued, err);
+            return;
+        }
+        if (tid == 0 && i + kAhead < nload) issue(i + kAhead), issued = i + kAhead;
+        const int ra = i - 1, rb = i - 3, rc = i - 5;  // local rows of levels 1, 2, 3
+        float4 v1[ITEMS], v2[ITEMS];
+        const bool do1 = ra >= 1 && ra <= yn + 4, do2 = rb >= 2 && rb <= yn + 3, do3 = rc >= 3 && rc <= yn + 2;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) v1[j] = vn[j];
+        load_v(ra + 1);  // for the next iteration
+        if (do1) {
+            float4 pn[ITEMS];
+            row_update(ring0 + ((ra + kSlots0 - 1) % kSlots0) * nx, ring0 + (ra % kSlots0) * nx,
+                       ring0 + ((ra + 1) % kSlots0) * nx, col, on, nq, nx, lane, v1, pn, k0);
+            float* l1 = ring1 + (ra % kSlots1) * nx;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (on[j]) *reinterpret_cast<float4*>(l1 + 4 * col[j]) = pn[j];
+        }
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) v2[j] = w1b[j];
+        if (do2) {
+            float4 pn[ITEMS];
+            row_update(ring1 + ((rb + kSlots1 - 1) % kSlots1) * nx, ring1 + (rb % kSlots1) * nx,
+                       ring1 + ((rb + 1) % kSlots1) * nx, col, on, nq, nx, lane, v2, pn, k1);
+            float* l2 = ring2 + (rb % kSlots2) * nx;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (on[j]) *reinterpret_cast<float4*>(l2 + 4 * col[j]) = pn[j];
+        }
+        if (do3) {
+            float4 pn[ITEMS], v3[ITEMS];
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) v3[j] = w2b[j];
+            row_update(ring2 + ((rc + kSlots2 - 1) % kSlots2) * nx, ring2 + (rc % kSlots2) * nx,
+                       ring2 + ((rc + 1) % kSlots2) * nx, col, on, nq, nx, lane, v3, pn, k2);
+            const size_t ro = (size_t)(y0 - 3 + rc) * nx;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if (!on[j]) continue;
+                stg4(phi_out + ro + 4 * col[j], pn[j]);
+                stg4(v_out + ro + 4 * col[j], v3[j]);
+            }
+        }
+        // the dphi each level hands down reaches the next level two iterations later
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            w1b[j] = w1a[j];
+            w1a[j] = v1[j];
+            w2b[j] = w2a[j];
+            w2a[j] = v2[j];
+        }
+    }
+}
+
+}  // namespace
+
+// The 2D three-step pass takes FP32 boxes with an x side that is a multiple of 128 up to
+// 4096 (at most two float4 per thread of a 512-thread CTA, 14 rows of rings in shared memory).
+bool t3_2d_ok(const Geo& g)
+{
+    return g.dims == 2 && g.nx % 128 == 0 && g.nx <= 2 * kT3Threads * 4 && g.ny >= 3;
+}
+
+cudaError_t launch_step_t3_2d(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
+                              KickF k0, KickF k1, KickF k2, RunConst<float> rc, unsigned int* err, cudaStream_t st)
+{
+    if (!t3_2d_ok(g)) return cudaErrorNotSupported;
+    const KickP p0 = kick_packed(k0, rc.deta), p1 = kick_packed(k1, rc.deta), p2 = kick_packed(k2, rc.deta);
+    const size_t sm = smem2d_t3(g.nx);
+    const int sms = sm_count_current();
+    const int cy = (g.ny + sms - 1) / sms;
+    const int blocks = (g.ny + cy - 1) / cy;
+    static std::atomic<unsigned long long> attr1{0}, attr2{0}, attr4{0};
+    if (g.nx / 4 > kT3Threads) {
+        cudaError_t e = smem_limit_once(attr2, (const void*)k_step2d_t3<2, 0>, (int)smem2d_t3(8 * kT3Threads));
+        if (e != cudaSuccess) return e;
+        e = smem_limit_once(attr4, (const void*)k_step2d_t3<2, 4096>, (int)smem2d_t3(4096));
+        if (e != cudaSuccess) return e;
+        if (g.nx == 4096)
+            k_step2d_t3<2, 4096>
+                <<<blocks, kT3Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, p0, p1, p2, err);
+        else
+            k_step2d_t3<2, 0>
+                <<<blocks, kT3Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, p0, p1, p2, err);
+    } else {
+        const cudaError_t e = smem_limit_once(attr1, (const void*)k_step2d_t3<1, 0>, (int)smem2d_t3(4 * kT3Threads));
+        if (e != cudaSuccess) return e;
+        k_step2d_t3<1, 0>
+            <<<blocks, kT3Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, p0, p1, p2, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace prs

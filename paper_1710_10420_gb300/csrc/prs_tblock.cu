@@ -256,8 +256,7 @@ static __device__ __noinline__ void drain_rows(uint64_t* bar, int from, int issu
 template <int ITEMS, int NX>
 __global__ void __launch_bounds__(kTb2Threads, 1)
     k_step2d_t2(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
-                  float* __restrict__ v_out, int nx_, int ny, int cy, KickF k0, KickF k1,
-                  RunConst<float> rc, unsigned int* err)
+                  float* __restrict__ v_out, int nx_, int ny, int cy, KickP p0, KickP p1, unsigned int* err)
 {
     const int nx = NX > 0 ? NX : nx_;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -288,10 +287,12 @@ __global__ void __launch_bounds__(kTb2Threads, 1)
         mbar_arrive_expect_tx(b, rowb);
         bulk_g2s(ring0 + (i % kR2Slots0) * nx, phi_in + (size_t)wy(y0 - 2 + i) * nx, rowb, b);
     };
-    // iteration t waits for rows 2t, 2t+1 and issues the two rows iteration t + kR2Ahead waits for
+    // iteration t waits for rows 2t, 2t+1 and issues the two rows iteration t + kR2Ahead waits for;
+    // before the first iteration every slot of the ring is free, so the rows of the first
+    // iterations are all in flight at once instead of one iteration's latency apart
     int issued = -1;
     if (tid == 0)
-        for (int i = 0; i < 2 * kR2Ahead && i < nload; ++i) issue(i), issued = i;
+        for (int i = 0; i < kR2Slots0 && i < nload; ++i) issue(i), issued = i;
 
     int col[ITEMS];
     bool on[ITEMS];
@@ -313,11 +314,14 @@ __global__ void __launch_bounds__(kTb2Threads, 1)
             if (on[j]) dst[j] = ldg_stream4(vp + 4 * col[j]);
     };
 
-    auto level1 = [&](int jr, const float4* vin, float4* vout) {
+    // ring slots by rotation: level-0 row r sits in slot r mod kR2Slots0, level-1 row r in slot
+    // r mod kR2Slots1; an iteration advances every row index by two
+    auto level1 = [&](int jr, int sm, const float4* vin, float4* vout) {  // sm = (jr - 1) mod kR2Slots0
         if (jr < 1 || jr > yn + 2) return;
-        const float* pm = ring0 + ((jr - 1) % kR2Slots0) * nx;
-        const float* pc = ring0 + (jr % kR2Slots0) * nx;
-        const float* pp = ring0 + ((jr + 1) % kR2Slots0) * nx;
+        const int sc = sm + 1 == kR2Slots0 ? 0 : sm + 1, sp = sc + 1 == kR2Slots0 ? 0 : sc + 1;
+        const float* pm = ring0 + sm * nx;
+        const float* pc = ring0 + sc * nx;
+        const float* pp = ring0 + sp * nx;
         float* l1 = ring1 + (jr % kR2Slots1) * nx;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
@@ -328,16 +332,17 @@ __global__ void __launch_bounds__(kTb2Threads, 1)
             const float4 ym = lds4(pm + 4 * col[j]);
             float4 pn;
             float4 vv = vin[j];
-            update4(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, k0, rc, false);
+            update4p<false>(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, p0);
             *reinterpret_cast<float4*>(l1 + 4 * col[j]) = pn;
             vout[j] = vv;
         }
     };
     auto level2 = [&](int kr, const float4* vin) {
         if (kr < 2 || kr > yn + 1) return;
-        const float* pm = ring1 + ((kr - 1) % kR2Slots1) * nx;
-        const float* pc = ring1 + (kr % kR2Slots1) * nx;
-        const float* pp = ring1 + ((kr + 1) % kR2Slots1) * nx;
+        const int sc = kr % kR2Slots1, sm = sc == 0 ? kR2Slots1 - 1 : sc - 1, sp = sc + 1 == kR2Slots1 ? 0 : sc + 1;
+        const float* pm = ring1 + sm * nx;
+        const float* pc = ring1 + sc * nx;
+        const float* pp = ring1 + sp * nx;
         const size_t ro = (size_t)(y0 - 2 + kr) * nx;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
@@ -348,13 +353,14 @@ __global__ void __launch_bounds__(kTb2Threads, 1)
             const float4 ym = lds4(pm + 4 * col[j]);
             float4 pn;
             float4 vv = vin[j];
-            update4(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, k1, rc, false);
+            update4p<false>(c, left, right, lds4(pp + 4 * col[j]), ym, ym, ym, vv, pn, p1);
             stg4(phi_out + ro + 4 * col[j], pn);
             stg4(v_out + ro + 4 * col[j], vv);
         }
     };
 
     const int tmax = (yn + 5) / 2;  // last iteration: level-2 row 2t-3 or 2t-4 reaches yn+1
+    int s0 = kR2Slots0 - 2;         // (2t - 2) mod kR2Slots0: slot of level-1 row 2t-1's row below
     for (int t = 0; t <= tmax; ++t) {
         bool ok = true;
         for (int i = 2 * t; i <= 2 * t + 1; ++i)  // rows 2t, 2t+1 (rows below were waited earlier)
@@ -366,14 +372,16 @@ __global__ void __launch_bounds__(kTb2Threads, 1)
         // rows 2(t+kR2Ahead) and the next, into the slots of rows 2t-4 and 2t-3 (last read by
         // level 1 at iteration t-1; level 1 now reads rows 2t-2 .. 2t+1)
         if (tid == 0)
-            for (int i = 2 * (t + kR2Ahead); i <= 2 * (t + kR2Ahead) + 1 && i < nload; ++i) issue(i), issued = i;
+            for (int i = max(issued + 1, 2 * (t + kR2Ahead)); i <= 2 * (t + kR2Ahead) + 1 && i < nload; ++i)
+                issue(i), issued = i;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) va0[j] = vb0[j], va1[j] = vb1[j];
         load_v(2 * t + 1, vb0);  // for iteration t+1: rows 2t+1, 2t+2
         load_v(2 * t + 2, vb1);
         float4 no[ITEMS], ne[ITEMS];
-        level1(2 * t - 1, va0, no);
-        level1(2 * t, va1, ne);
+        const int s1 = s0 + 1 == kR2Slots0 ? 0 : s0 + 1;  // (2t - 1) mod kR2Slots0
+        level1(2 * t - 1, s0, va0, no);
+        level1(2 * t, s1, va1, ne);
         level2(2 * t - 4, e0);
         level2(2 * t - 3, o0);
 #pragma unroll
@@ -382,6 +390,8 @@ __global__ void __launch_bounds__(kTb2Threads, 1)
             e1[j] = ne[j];
             o0[j] = no[j];
         }
+        s0 += 2;
+        if (s0 >= kR2Slots0) s0 -= kR2Slots0;
     }
 }
 
@@ -496,6 +506,7 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
 {
     if (g.dims == 2) {
         if (phi_mid || v_mid) return cudaErrorNotSupported;
+        const KickP p0 = kick_packed(k0, rc.deta), p1 = kick_packed(k1, rc.deta);
         static std::atomic<unsigned long long> attr1{0}, attr2{0};
         const size_t sm = smem2d_t2(g.nx);
         const int sms = sm_count_current();
@@ -509,17 +520,17 @@ cudaError_t launch_step_t2(const Geo& g, const float* phi_in, float* phi_out, co
             const cudaError_t e4 = smem_limit_once(attr4, (const void*)k_step2d_t2<2, 4096>, (int)smem2d_t2(4096));
             if (e4 != cudaSuccess) return e4;
             if (g.nx == 4096)
-                k_step2d_t2<2, 4096><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0,
-                                                                      k1, rc, err);
+                k_step2d_t2<2, 4096>
+                    <<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, p0, p1, err);
             else
-                k_step2d_t2<2, 0><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
-                                                                   rc, err);
+                k_step2d_t2<2, 0>
+                    <<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, p0, p1, err);
         } else {
             const cudaError_t e =
                 smem_limit_once(attr1, (const void*)k_step2d_t2<1, 0>, (int)smem2d_t2(4 * kTb2Threads));
             if (e != cudaSuccess) return e;
-            k_step2d_t2<1, 0><<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, k0, k1,
-                                                            rc, err);
+            k_step2d_t2<1, 0>
+                <<<blocks, kTb2Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, p0, p1, err);
         }
         return cudaGetLastError();
     }

@@ -79,7 +79,8 @@ __device__ __forceinline__ void update4(float4 c, float left, float right, float
 }
 
 // update4 with the constants already packed (KickP): the same operations in the same order,
-// so the same bits.
+// so the same bits.  THREE_D = false: the 2D update (zp, zm unused).
+template <bool THREE_D = true>
 __device__ __forceinline__ void update4p(float4 c, float left, float right, float4 yp, float4 ym, float4 zp,
                                          float4 zm, float4& v, float4& pn, const KickP& k)
 {
@@ -88,8 +89,10 @@ __device__ __forceinline__ void update4p(float4 c, float left, float right, floa
     f2 s1 = pk2(__fadd_rn(c.w, c.y), __fadd_rn(right, c.z));
     s0 = add2(s0, add2(pk2(yp.x, yp.y), pk2(ym.x, ym.y)));
     s1 = add2(s1, add2(pk2(yp.z, yp.w), pk2(ym.z, ym.w)));
-    s0 = add2(s0, add2(pk2(zp.x, zp.y), pk2(zm.x, zm.y)));
-    s1 = add2(s1, add2(pk2(zp.z, zp.w), pk2(zm.z, zm.w)));
+    if (THREE_D) {
+        s0 = add2(s0, add2(pk2(zp.x, zp.y), pk2(zm.x, zm.y)));
+        s1 = add2(s1, add2(pk2(zp.z, zp.w), pk2(zm.z, zm.w)));
+    }
     const f2 c0 = pk2(c.x, c.y), c1 = pk2(c.z, c.w);
     const f2 u0 = mul2(c0, fma2(nk2, mul2(c0, c0), kk1));
     const f2 u1 = mul2(c1, fma2(nk2, mul2(c1, c1), kk1));

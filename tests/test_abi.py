@@ -87,26 +87,28 @@ def test_host_coefficients_follow_eq6():
 
 def test_default_steps_per_pass(lib):
     """The library's default steps per pass (host logic): two for FP32 3D boxes whose x side is
-    a multiple of 128 and whose two-step tiles get at least 4 rows of y, and for FP32 2D boxes of
-    at least 2^24 sites; one otherwise (L2-sized 2D states, FP64, boxes the staged kernels do not
-    take, a prime y side)."""
+    a multiple of 128 and whose two-step tiles get at least 4 rows of y; for FP32 2D boxes of at
+    least 2^24 sites three on rows wider than 2048 and two on narrower ones; one otherwise
+    (L2-sized 2D states, FP64, boxes the staged kernels do not take, a prime y side)."""
     cases = [((512, 512, 512), prs.PRS_FP32, 2), ((128, 128, 128), prs.PRS_FP32, 2),
              ((256, 256, 1024), prs.PRS_FP32, 2), ((1024, 1024, 1024), prs.PRS_FP32, 2),
-             ((1024, 1024, 256), prs.PRS_FP32, 2), ((4096, 4096), prs.PRS_FP32, 2),
+             ((1024, 1024, 256), prs.PRS_FP32, 2), ((4096, 4096), prs.PRS_FP32, 3),
              ((2048, 2048), prs.PRS_FP32, 1), ((512, 512, 512), prs.PRS_FP64, 1),
              ((500, 500, 500), prs.PRS_FP32, 1), ((4096, 4096), prs.PRS_FP64, 1),
-             ((256, 251, 64), prs.PRS_FP32, 1), ((384, 96, 32), prs.PRS_FP32, 2)]
+             ((256, 251, 64), prs.PRS_FP32, 1), ((384, 96, 32), prs.PRS_FP32, 2),
+             ((2048, 8192), prs.PRS_FP32, 2), ((4096, 8192), prs.PRS_FP32, 3)]
     for shape, precision, want in cases:
         assert prs.prs_default_tblock(prs.make_params(shape, precision=precision)) == want, shape
 
 
 def test_max_steps_per_pass(lib):
     """The most steps one pass fuses: three for FP32 3D boxes of the three-step pass (x sides that are
-    multiples of 128, y sides multiples of 8 of at least 16), two for FP32 2D boxes of the two-step
-    pass, one for FP64 and boxes the staged kernels do not take; never below the default."""
+    multiples of 128, y sides multiples of 8 of at least 16) and FP32 2D boxes of the 2D three-step
+    pass (x sides that are multiples of 128 up to 4096), one for FP64 and boxes the staged kernels do
+    not take; never below the default."""
     cases = [((512, 512, 512), prs.PRS_FP32, 3), ((128, 128, 128), prs.PRS_FP32, 3),
              ((1024, 1024, 1024), prs.PRS_FP32, 3), ((384, 96, 32), prs.PRS_FP32, 3),
-             ((4096, 4096), prs.PRS_FP32, 2), ((2048, 2048), prs.PRS_FP32, 2),
+             ((4096, 4096), prs.PRS_FP32, 3), ((2048, 2048), prs.PRS_FP32, 3), ((128, 3), prs.PRS_FP32, 3),
              ((512, 512, 512), prs.PRS_FP64, 1), ((500, 500, 500), prs.PRS_FP32, 1),
              ((4096, 4096), prs.PRS_FP64, 1)]
     for shape, precision, want in cases:

@@ -399,17 +399,21 @@ def test_full_size_3d_1024_sampled(tblock, nsteps):
     assert worst <= 1e-5  # |phi| < 1.1: absolute ~ relative
 
 
-@pytest.mark.parametrize("tblock", [0, 2])
-def test_full_size_2d_4096_sampled(tblock):
-    """2D 4096^2 FP32 (0: the library default; 2: two-step passes): sampled sites after 6 steps."""
-    worst = _sampled_step_check((4096, 4096), 6, tblock)
+@pytest.mark.parametrize("tblock,nsteps", [(0, 6), (2, 6), (3, 7)])
+def test_full_size_2d_4096_sampled(tblock, nsteps):
+    """2D 4096^2 FP32 (0: the library default; 2: two-step passes; 3: two three-step passes and a
+    single step): sampled sites after nsteps steps."""
+    worst = _sampled_step_check((4096, 4096), nsteps, tblock)
     assert worst <= 1e-5
 
 
-def test_two_step_passes_match_single_steps_2d():
-    shape = (4096, 64)
+@pytest.mark.parametrize("tblock", [2, 3])
+@pytest.mark.parametrize("shape", [(4096, 64), (2048, 152), (512, 40)])
+def test_multi_step_passes_match_single_steps_2d(shape, tblock):
+    """2D two- and three-step passes against one-step passes over many passes (whole rows of up to
+    4096 columns; chunks of one row to several per SM)."""
     a = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=1)
-    b = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=2)
+    b = _run(shape, prs.PRS_FP32, 40, None, None, seed=3, tblock=tblock)
     assert _rel(b[0], a[0].astype(np.float64)) <= 1e-5 and _rel(b[1], a[1].astype(np.float64)) <= 1e-5
 
 
