@@ -14,10 +14,14 @@
 // every lane, as the first version did, cost about a tenth of all instructions of the
 // pass (each lane's copy is serialised through uniform registers).
 //
-// The register queues along z (level 0 at planes j-1, j, j+1 and level 1 at k-1, k, k+1)
-// rotate by moves: unrolling the plane loop three times, so that they rotate by renaming,
-// spilled at the 96-register limit of two 320-thread CTAs per SM and measured slower
-// (1.556 against 1.508 ms per step at 1024^3).
+// Only the planes that have left the shared-memory rings stay in registers (level 0 at plane
+// j-1, level 1 at k-1, the level-1 dphi handed to level 2); the stencil reads the others in
+// the rings, where it reads their neighbours anyway.  (Full register queues along z, rotated
+// by moves or, with the plane loop unrolled three times, by renaming, spilled at the
+// 96-register limit of two 320-thread CTAs per SM.)  The plane loop's steady-state body tests
+// no plane ranges, the kick constants arrive packed as f32x2 operands, the copy context sits
+// in shared memory and x-edge values are loaded by the two lanes that use them: together 22%
+// fewer instructions than the plain loop, which leaves the pass waiting on its copies.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
