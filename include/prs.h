@@ -104,10 +104,12 @@ typedef struct {
     double phi0;       /* vacuum value (> 0)                                        */
     uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
     uint32_t flags;    /* PRS_REPRO | PRS_FP32_CR | PRS_DEBUG, or 0                 */
-    int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (2 for
-                          FP32 3D boxes whose two-step tiles get at least 4 rows of y;
-                          for FP32 2D boxes of at least 2^24 sites 3 on rows wider than
-                          2048, else 2; else 1; see prs_default_tblock); 2 = two-step passes for FP32 boxes with
+    int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (FP32
+                          3D: 3 up to 2^22 sites on boxes of the three-step pass, else 2
+                          where the two-step tiles get at least 4 rows of y; FP32 2D
+                          below 2^24 sites: 3 with at most 1024 rows, else 1; from 2^24
+                          sites: 3 on rows wider than 2048, else 2; otherwise 1; see
+                          prs_default_tblock); 2 = two-step passes for FP32 boxes with
                           an x side that is a multiple of 128 (3D; z side >= 3) or a
                           multiple of 128 up to 4096 (2D), else 1; 3 = three-step
                           passes for FP32 3D boxes with an x side that is a multiple

@@ -31,23 +31,26 @@ cudaError_t launch_step_t3(const Geo& g, const float* phi_in, float* phi_out, co
     return launch_step_t3_tma(g, phi_in, phi_out, v_in, v_out, k0, k1, k2, rc, err, st);
 }
 
-// The library's default number of steps per pass.  FP32 3D: two wherever the two-step
-// pass gets tiles of at least 4 rows (fewer rows make level 1 recompute more than it
-// saves) — per step against one step per pass, measured 13.6 against 22.7 us at 128^3,
-// 38.2 against 48.2 us at 256^3, 0.230 against 0.323 ms at 512^3 and 1.67 against 2.53 ms
-// at 1024^3.  FP32 2D, once the state (three fields) outgrows L2: three on rows wider than
-// 2048 (every thread of the 512-thread row kernels holds two float4; 4096^2: 22.6 us per step
-// against 25.7 two at a time and 47.0 one at a time), else two — rows are whole, so the levels
-// recompute only the rows outside each chunk; an L2-resident state (2048^2) steps about as
-// fast one step at a time (10.3 against 11.0 and 10.3 us).  FP64 and other boxes: one.
+// The library's default number of steps per pass.  Small states are bound by each pass's
+// latency rather than by bandwidth, so more steps per pass pay there most.  FP32 3D: three up
+// to 2^22 sites (128^3: 11.6 us per step against 15.5 two at a time and 21.7 one at a time;
+// 256 x 128^2: 13.4 against 14.4 and 22.5), else two wherever the two-step pass gets tiles of at
+// least 4 rows (256^3: 32.9 against 34.5 three and 48 one at a time; 1024^3: 1.37 against 1.43
+// and 2.53 ms).  FP32 2D below 2^24 sites: three when the box has at most 1024 rows (one CTA
+// marches a few of them: 256^2 3.8 against 8.2 us one at a time, 1024^2 6.2 against 8.2,
+// 2048 x 512 5.1 against 8.2), else one (2048^2 10.3 both, 512 x 2048 8.2 against 8.9); from 2^24
+// sites (state above L2) three on rows wider than 2048 (every thread of the 512-thread row
+// kernels holds two float4; 4096^2: 22.6 us against 25.7 two and 47.0 one at a time), else two.
+// FP64 and other boxes: one.
 int default_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)repro;
     if (precision != PRS_FP32 || !tblock_ok(g, precision)) return 1;
     if (g.dims == 2) {
-        if (g.S < (int64_t)1 << 24) return 1;
+        if (g.S < (int64_t)1 << 24) return t3_2d_ok(g) && g.ny <= 1024 ? 3 : 1;
         return t3_2d_ok(g) && g.nx > 2048 ? 3 : 2;
     }
+    if (t3tma_ok(g) && g.S <= (int64_t)1 << 22) return 3;
     return tblock3_rows(g) >= 4 ? 2 : 1;
 }
 

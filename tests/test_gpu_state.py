@@ -112,8 +112,8 @@ def test_default_passes_take_a_triple_for_odd_counts(owned):
     dphi at home after every call; the field follows the oracle either way."""
     import torch
 
-    shape = (384, 16, 24)
-    calls = (19, 3, 1, 5, 2, 7)
+    shape = (128, 16, 2056)  # above 2^22 sites: two steps per pass by default
+    calls = (3, 5, 2, 7)
     p = prs.make_params(shape, seed=6)
     assert prs.prs_default_tblock(p) == 2 and prs.prs_max_tblock(p) == 3
     fshape = tuple(reversed(shape))
