@@ -151,13 +151,14 @@ def test_debug_reports_a_nonfinite_state():
     _still_works()
 
 
-@pytest.mark.parametrize("shape", [(4096, 40), (512, 96), (256, 64, 24), (128, 32, 8)])
-def test_debug_two_step_passes_stay_in_bounds(shape):
-    """Two-step passes (2D and 3D) under PRS_DEBUG: the guard bands around the fields stay
-    intact and the state matches one step per pass to FP32 rounding (7 steps: three pairs,
-    then the single step that brings dphi back to the run's buffer)."""
+@pytest.mark.parametrize("tblock", [2, 3])
+@pytest.mark.parametrize("shape", [(4096, 40), (512, 96), (256, 64, 24), (128, 32, 8), (128, 32, 40)])
+def test_debug_multi_step_passes_stay_in_bounds(shape, tblock):
+    """Two- and three-step passes (2D and 3D) under PRS_DEBUG: the guard bands around the fields
+    stay intact and the state matches one step per pass to FP32 rounding (7 steps: three pairs or
+    two triples, then the single step that brings dphi back to the run's buffer)."""
     out = []
-    for flags, tb in ((prs.PRS_DEBUG, 2), (0, 1)):
+    for flags, tb in ((prs.PRS_DEBUG, tblock), (0, 1)):
         h = _raw_run(shape, flags, tblock=tb)
         try:
             assert prs.load().prs_step(h, 7) == prs.PRS_OK, prs.prs_last_error()
