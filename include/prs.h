@@ -105,11 +105,10 @@ typedef struct {
     uint64_t seed;     /* seed of the random initial field (prs_init with NULL)     */
     uint32_t flags;    /* PRS_REPRO | PRS_FP32_CR | PRS_DEBUG, or 0                 */
     int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (FP32
-                          3D: 3 up to 2^22 sites on boxes of the three-step pass, else 2
-                          where the two-step tiles get at least 4 rows of y; FP32 2D
-                          below 2^24 sites: 3 with at most 1024 rows, else 1; from 2^24
-                          sites: 3 on rows wider than 2048, else 2; otherwise 1; see
-                          prs_default_tblock); 2 = two-step passes for FP32 boxes with
+                          3D: 1 below 2^24 sites, else 2 where the two-step tiles get at
+                          least 4 rows of y; FP32 2D: 3 on rows of 2048 or more and on
+                          1024-wide rows of boxes with at most 1024 rows, else 2 from
+                          2^24 sites and 1 below; otherwise 1; see prs_default_tblock); 2 = two-step passes for FP32 boxes with
                           an x side that is a multiple of 128 (3D; z side >= 3) or a
                           multiple of 128 up to 4096 (2D), else 1; 3 = three-step
                           passes for FP32 3D boxes with an x side that is a multiple

@@ -31,26 +31,23 @@ cudaError_t launch_step_t3(const Geo& g, const float* phi_in, float* phi_out, co
     return launch_step_t3_tma(g, phi_in, phi_out, v_in, v_out, k0, k1, k2, rc, err, st);
 }
 
-// The library's default number of steps per pass.  Small states are bound by each pass's
-// latency rather than by bandwidth, so more steps per pass pay there most.  FP32 3D: three up
-// to 2^22 sites (128^3: 11.6 us per step against 15.5 two at a time and 21.7 one at a time;
-// 256 x 128^2: 13.4 against 14.4 and 22.5), else two wherever the two-step pass gets tiles of at
-// least 4 rows (256^3: 32.9 against 34.5 three and 48 one at a time; 1024^3: 1.37 against 1.43
-// and 2.53 ms).  FP32 2D below 2^24 sites: three when the box has at most 1024 rows (one CTA
-// marches a few of them: 256^2 3.8 against 8.2 us one at a time, 1024^2 6.2 against 8.2,
-// 2048 x 512 5.1 against 8.2), else one (2048^2 10.3 both, 512 x 2048 8.2 against 8.9); from 2^24
-// sites (state above L2) three on rows wider than 2048 (every thread of the 512-thread row
-// kernels holds two float4; 4096^2: 22.6 us against 25.7 two and 47.0 one at a time), else two.
-// FP64 and other boxes: one.
+// The library's default number of steps per pass (us per step, one / two / three steps per
+// pass).  FP32 3D: one below 2^24 sites, where a one-step pass cut into chunks of a few planes
+// occupies the GPU best (128^3 8.3 / 15.4 / 11.0, 256^2 x 128 18.1 / 21.6 / 20.5); from 2^24 two
+// wherever the two-step pass gets tiles of at least 4 rows (256^3 46.7 / 32.8 / 34.3; 1024^3
+// 2.53 / 1.37 / 1.43 ms).  FP32 2D: three on rows of 2048 or more (2048^2 10.3 / 10.3 / 9.4,
+// 4096^2 47.0 / 25.7 / 22.6) and on 1024-wide rows when the box has at most 1024 of them (1024^2
+// 6.2 / 6.2 / 5.8); else two from 2^24 sites (state above L2) and one below (512^2 4.1 / 5.1 /
+// 4.6).  FP64 and other boxes: one.
 int default_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)repro;
     if (precision != PRS_FP32 || !tblock_ok(g, precision)) return 1;
     if (g.dims == 2) {
-        if (g.S < (int64_t)1 << 24) return t3_2d_ok(g) && g.ny <= 1024 ? 3 : 1;
-        return t3_2d_ok(g) && g.nx > 2048 ? 3 : 2;
+        if (t3_2d_ok(g) && (g.nx >= 2048 || (g.nx >= 1024 && g.ny <= 1024))) return 3;
+        return g.S >= (int64_t)1 << 24 ? 2 : 1;
     }
-    if (t3tma_ok(g) && g.S <= (int64_t)1 << 22) return 3;
+    if (g.S < (int64_t)1 << 24) return 1;
     return tblock3_rows(g) >= 4 ? 2 : 1;
 }
 
