@@ -107,8 +107,8 @@ typedef struct {
     int32_t tblock;    /* leapfrog steps per pass over HBM: 0 = library's choice (FP32
                           3D: 1 below 2^24 sites, else 2 where the two-step tiles get at
                           least 4 rows of y; FP32 2D: 3 on rows of 2048 or more and on
-                          1024-wide rows of boxes with at most 1024 rows, else 2 from
-                          2^24 sites and 1 below; otherwise 1; see prs_default_tblock); 2 = two-step passes for FP32 boxes with
+                          boxes of at most 1024 rows, else 2 from 2^24 sites and 1
+                          below; otherwise 1; see prs_default_tblock); 2 = two-step passes for FP32 boxes with
                           an x side that is a multiple of 128 (3D; z side >= 3) or a
                           multiple of 128 up to 4096 (2D), else 1; 3 = three-step
                           passes for FP32 3D boxes with an x side that is a multiple

@@ -36,15 +36,15 @@ cudaError_t launch_step_t3(const Geo& g, const float* phi_in, float* phi_out, co
 // occupies the GPU best (128^3 8.3 / 15.4 / 11.0, 256^2 x 128 18.1 / 21.6 / 20.5); from 2^24 two
 // wherever the two-step pass gets tiles of at least 4 rows (256^3 46.7 / 32.8 / 34.3; 1024^3
 // 2.53 / 1.37 / 1.43 ms).  FP32 2D: three on rows of 2048 or more (2048^2 10.3 / 10.3 / 9.4,
-// 4096^2 47.0 / 25.7 / 22.6) and on 1024-wide rows when the box has at most 1024 of them (1024^2
-// 6.2 / 6.2 / 5.8); else two from 2^24 sites (state above L2) and one below (512^2 4.1 / 5.1 /
-// 4.6).  FP64 and other boxes: one.
+// 4096^2 47.0 / 25.7 / 22.6) and on boxes of at most 1024 rows (256^2 4.1 / 4.6 / 3.4, 1024^2
+// 6.2 / 6.2 / 5.8; 512^2 is the exception, 4.1 / 5.1 / 4.6); else two from 2^24 sites (state above
+// L2) and one below (512 x 2048 8.2 / 8.9 / -).  FP64 and other boxes: one.
 int default_fused_steps(const Geo& g, int precision, bool repro)
 {
     (void)repro;
     if (precision != PRS_FP32 || !tblock_ok(g, precision)) return 1;
     if (g.dims == 2) {
-        if (t3_2d_ok(g) && (g.nx >= 2048 || (g.nx >= 1024 && g.ny <= 1024))) return 3;
+        if (t3_2d_ok(g) && (g.nx >= 2048 || g.ny <= 1024)) return 3;
         return g.S >= (int64_t)1 << 24 ? 2 : 1;
     }
     if (g.S < (int64_t)1 << 24) return 1;

@@ -88,7 +88,7 @@ def test_host_coefficients_follow_eq6():
 def test_default_steps_per_pass(lib):
     """The library's default steps per pass (host logic): FP32 3D, one below 2^24 sites, else two
     where the two-step tiles get at least 4 rows of y; FP32 2D, three on rows of 2048 or more and on
-    1024-wide rows of boxes with at most 1024 rows, else two from 2^24 sites and one below; one
+    boxes of at most 1024 rows, else two from 2^24 sites and one below; one
     otherwise (FP64, boxes the staged kernels do not take, a prime y side)."""
     cases = [((512, 512, 512), prs.PRS_FP32, 2), ((128, 128, 128), prs.PRS_FP32, 1),
              ((256, 128, 128), prs.PRS_FP32, 1), ((256, 256, 256), prs.PRS_FP32, 2),
@@ -98,7 +98,7 @@ def test_default_steps_per_pass(lib):
              ((500, 500, 500), prs.PRS_FP32, 1), ((4096, 4096), prs.PRS_FP64, 1),
              ((256, 251, 64), prs.PRS_FP32, 1), ((384, 96, 32), prs.PRS_FP32, 1),
              ((2048, 8192), prs.PRS_FP32, 3), ((4096, 8192), prs.PRS_FP32, 3), ((1024, 16384), prs.PRS_FP32, 2),
-             ((256, 256), prs.PRS_FP32, 1), ((1024, 1024), prs.PRS_FP32, 3), ((512, 2048), prs.PRS_FP32, 1),
+             ((256, 256), prs.PRS_FP32, 3), ((1024, 1024), prs.PRS_FP32, 3), ((512, 2048), prs.PRS_FP32, 1),
              ((1024, 4096), prs.PRS_FP32, 1), ((2048, 512), prs.PRS_FP32, 3), ((384, 128, 512), prs.PRS_FP32, 2)]
     for shape, precision, want in cases:
         assert prs.prs_default_tblock(prs.make_params(shape, precision=precision)) == want, shape
