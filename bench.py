@@ -589,7 +589,9 @@ def run_batch_figure(prs, stream, dev, scale: float) -> dict:
             "site_updates": total, "batched_s": ms_batch / 1e3, "one_at_a_time_s": ms_seq / 1e3,
             "batched_value": total / (ms_batch / 1e3), "one_at_a_time_value": total / (ms_seq / 1e3),
             "unit": "site-updates/s", "speedup": ms_seq / ms_batch, "create_s": t_create,
-            "tuned_tile_len": tl, "tuned_group_bytes": budget, "first_output_run0": list(out[0, 0])}
+            "tuned_tile_len": tl, "tile_len_0": "a class of boxes stepped alone (2^22 sites and more, multi-step "
+            "passes), after the persistent launch of the others", "tuned_group_bytes": budget,
+            "first_output_run0": list(out[0, 0])}
 
 
 def run_adjoint_figure(prs, stream, dev, nsteps: int = 1270) -> dict:

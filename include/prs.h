@@ -275,11 +275,16 @@ int prs_destroy(prs_sim* sim);
 /* Create an ensemble of nruns runs (each validated as by prs_create), allocate all
  * fields, pick a tile length for each geometry class of runs (4 to 32 planes or bands)
  * and the L2 grouping by timing short trials on them (the autotuner), then set every
- * run to its seeded random initial condition (step 0).  stream may be NULL (the
- * ensemble then creates its own stream). */
+ * run to its seeded random initial condition (step 0).  A run of 2^22 sites or more
+ * that the library steps with multi-step passes (prs_default_tblock >= 2) fills the
+ * GPU by itself: it is stepped alone, after the persistent launch of the others, as
+ * prs_step_measure would step it (its fields and outputs are those of the same run
+ * stepped alone; the run holds a second dphi buffer like a prs_sim).  stream may be
+ * NULL (the ensemble then creates its own stream). */
 int prs_batch_create(const prs_params* runs, int nruns, void* stream, prs_batch** out);
 
-/* Advance run r by nsteps_per_run[r] (>= 0) steps in one persistent launch.  With
+/* Advance run r by nsteps_per_run[r] (>= 0) steps: one persistent launch for the runs
+ * it holds, then the runs stepped alone, all on the ensemble's stream.  With
  * measure_every > 0, the diagnostics of run r at its steps n, n+m, ... (n its
  * step at the call, up to n + nsteps_per_run[r]) are written to
  *   out_series[(r*out_capacity + k)*4 + {0,1,2,3}] = {step, A/V, gamma v, n_links}
@@ -297,7 +302,7 @@ int prs_batch_get_state(prs_batch* batch, int run, void* h_phi, void* h_dphi, in
 int prs_batch_set_state(prs_batch* batch, int run, const void* h_phi, const void* h_dphi, int64_t n);
 
 /* The autotuner's choice: tile length of `run` (bands of 4096/x rows in 2D,
- * z-planes in 3D) and the bytes of fields per L2 group. */
+ * z-planes in 3D; 0 for a run stepped alone) and the bytes of fields per L2 group. */
 int prs_batch_tuning(prs_batch* batch, int run, int* tile_len, double* group_bytes);
 
 /* Release the ensemble and everything it allocated. */

@@ -649,6 +649,39 @@ static int prs_step_measure_impl(prs_sim* s, int64_t nsteps, prs_diag* out)
     return s->h_status->result.n_nonfinite ? PRS_ENONFINITE : PRS_OK;
 }
 
+int prs::step_measure_async(prs_sim* s, int64_t nsteps, DiagAcc* result)
+{
+    if (!s || !result || nsteps < 0) return PRS_EINVAL;
+    if (!s->initialised) return PRS_ESTATE;
+    if (nsteps > 0 && !cfl_ok_over(s->p, s->n, nsteps)) return PRS_EINVAL;
+    DiagScratch scr = s->scr;
+    scr.result = result;
+    const RunConst<float> rc{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
+                             (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
+    cudaError_t e = cudaErrorNotSupported;
+    if (nsteps > 0 && fast_diag_ok(s)) {
+        double c[5];
+        step_coefficients(s->p, s->n, c);
+        e = launch_step_measure_fast(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
+                                     (const float*)s->dphi, (float*)s->dphi, kick_f32(c, s->rc), rc, scr,
+                                     &s->d_status->error, s->stream);
+        if (e == cudaSuccess) {
+            s->cur = 1 - s->cur;
+            s->n += 1;
+            return prs_step_impl(s, nsteps - 1);
+        }
+        if (e != cudaErrorNotSupported) return cuda_fail(e, "step_measure_async launch");
+    }
+    e = cudaErrorNotSupported;
+    if (fast_diag_ok(s))
+        e = launch_measure_fast(s->g, (const float*)s->phi[s->cur], (const float*)s->dphi, rc, scr,
+                                &s->d_status->error, s->stream);
+    if (e == cudaErrorNotSupported)
+        e = launch_measure(s->g, s->p.precision, s->phi[s->cur], s->dphi, s->rc, scr, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step_measure_async launch");
+    return prs_step_impl(s, nsteps);
+}
+
 static int prs_measure_ex_impl(prs_sim* s, prs_diag* out)
 {
     if (!s || !out) return PRS_EINVAL;

@@ -24,6 +24,16 @@
 //    candidates at creation (the autotuner).  The persistent launch is captured
 //    once into a CUDA graph and replayed while the step counts stay the same; the
 //    counters are reset and the per-step coefficients uploaded before each replay.
+//  * Runs stepped alone: a run whose box fills the GPU by itself (2^22 sites or more)
+//    and that the library steps with multi-step passes stays out of the persistent
+//    kernel.  It gains nothing from sharing the GPU, and its multi-step passes move a
+//    half or a third of the bytes of one-step items (2048^2: 9.4 us per step with three
+//    steps per pass against 11.4 us as one-step items).  Such a run gets a single-run
+//    handle bound to its fields and is stepped after the persistent launch, on the same
+//    stream, per output interval by the fused diagnostics pass and the library's passes,
+//    its outputs written into the same result array: fields and outputs are those of the
+//    run stepped alone through prs_step_measure.  A fixed rule, not a timed choice, so
+//    that two ensembles of the same runs give the same fields.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -267,6 +277,7 @@ struct prs_batch {
     size_t work_bytes;
     unsigned int* d_err;     // error word + abort flag + ticket counter live here
     unsigned int* h_err;
+    std::vector<prs_sim*> solo;  // per run: its handle when stepped alone, else null
     cudaGraphExec_t graph;
     std::vector<int64_t> graph_nsteps;
     int64_t graph_measure;
@@ -331,13 +342,14 @@ static void plan(const prs_batch* b, const int64_t* nsteps, int64_t measure_ever
             u.ntiles = (g.ny + u.len - 1) / u.len;
         }
         u.measure_every = (int)measure_every;
-        u.nitems = nsteps[r] + 1;
+        const bool alone = b->solo[r] != nullptr;  // no items in the persistent kernel
+        u.nitems = alone ? 0 : nsteps[r] + 1;
         u.nout = measure_every > 0 ? (int)(nsteps[r] / measure_every) + 1 : 0;
         const double* rcd = &b->rc[6 * (size_t)r];
         u.rc = RunConst<float>{(float)rcd[0], (float)rcd[1], (float)rcd[2], (float)rcd[3], (float)rcd[4],
                                (float)rcd[5]};
         S.coef_off[r] = S.coef.size();
-        for (int64_t k = 0; k < nsteps[r]; ++k) {
+        for (int64_t k = 0; k < (alone ? 0 : nsteps[r]); ++k) {
             double c[5];
             step_coefficients(b->p[r], b->n[r] + k, c);
             const KickF kf = kick_f32(c, rcd);
@@ -359,6 +371,7 @@ static void plan(const prs_batch* b, const int64_t* nsteps, int64_t measure_ever
     std::vector<std::vector<int>> groups;
     double acc = 0.0;
     for (int r = 0; r < R; ++r) {
+        if (b->solo[r]) continue;
         const double fb = 3.0 * (double)b->g[r].S * sizeof(float);
         if (groups.empty() || acc + fb > budget) {
             groups.emplace_back();
@@ -488,6 +501,69 @@ static int run_schedule(prs_batch* b, const int64_t* nsteps, int64_t measure_eve
     return batch_cuda(cudaGetLastError(), "batch launch");
 }
 
+// Runs stepped alone: boxes of 2^22 sites or more that the library steps with multi-step
+// passes (the ensemble's runs are FP32).
+static bool steps_alone(const Geo& g)
+{
+    return g.S >= ((int64_t)1 << 22) && default_fused_steps(g, PRS_FP32, false) >= 2;
+}
+
+// A run stepped alone: its handle follows the batch's view of the run (which field buffer
+// holds phi^n, the step count) before it steps, and the batch takes the buffer back after.
+static void solo_sync_in(prs_batch* b, int r)
+{
+    prs_sim* s = b->solo[r];
+    s->cur = b->cur[r];
+    s->n = b->n[r];
+}
+
+static int solo_make(prs_batch* b, int r)
+{
+    prs_sim* s = nullptr;
+    int rc = prs_create(&b->p[r], b->stream, &s);
+    if (!rc) rc = prs_bind(s, b->phi0[r], b->phi1[r], b->v[r]);
+    if (!rc) {
+        s->cur = b->cur[r];  // phi[0] = phi0, phi[1] = phi1: no copy below
+        rc = prs_set_state_device(s, b->cur[r] == 0 ? b->phi0[r] : b->phi1[r], b->v[r], b->n[r]);
+    }
+    if (rc) {
+        if (s) prs_destroy(s);
+        return rc;
+    }
+    b->solo[r] = s;
+    return PRS_OK;
+}
+
+// Queue the runs stepped alone, after the persistent launch: with outputs, per output the
+// diagnostics of the state (into the run's result slot) fused into the first of the steps up
+// to the next output; else the steps.  Leaves b->cur to the caller (solo_take_back).
+static int solo_queue(prs_batch* b, const int64_t* nsteps, int64_t measure_every, const Schedule& S)
+{
+    for (int r = 0; r < (int)b->p.size(); ++r) {
+        prs_sim* s = b->solo[r];
+        if (!s) continue;
+        solo_sync_in(b, r);
+        int rc = PRS_OK;
+        if (measure_every > 0) {
+            DiagAcc* res = (DiagAcc*)((char*)b->work + S.res_off[r]);
+            for (int k = 0; k < S.runs[r].nout && !rc; ++k) {
+                const int64_t left = nsteps[r] - (int64_t)k * measure_every;
+                rc = step_measure_async(s, left < measure_every ? left : measure_every, res + k);
+            }
+        } else {
+            rc = prs_step(s, nsteps[r]);
+        }
+        if (rc) return rc;
+    }
+    return PRS_OK;
+}
+
+static void solo_take_back(prs_batch* b)
+{
+    for (int r = 0; r < (int)b->p.size(); ++r)
+        if (b->solo[r]) b->cur[r] = b->solo[r]->cur;
+}
+
 // Times one candidate layout on the batch's fields for a few steps.
 static double trial(prs_batch* b, double budget, int steps)
 {
@@ -498,7 +574,7 @@ static double trial(prs_batch* b, double budget, int steps)
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, b->stream);
-    int rc = run_schedule(b, ns.data(), 0, budget, S, false);
+    int rc = run_schedule(b, ns.data(), 0, budget, S, false);  // the runs stepped alone sit out
     cudaEventRecord(e1, b->stream);
     cudaEventSynchronize(e1);
     float ms = 1e30f;
@@ -506,7 +582,7 @@ static double trial(prs_batch* b, double budget, int steps)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (int r = 0; r < R; ++r)
-        if (steps & 1) b->cur[r] ^= 1;
+        if ((steps & 1) && !b->solo[r]) b->cur[r] ^= 1;
     return rc == PRS_OK ? ms : 1e30;
 }
 
@@ -543,6 +619,7 @@ static void autotune(prs_batch* b)
     for (int r = 0; r < R; ++r) b->len[r] = 16;  // the best layout of full runs measured (see above)
     double best = cost(1e18);
     for (size_t c = 0; c < reps.size(); ++c) {
+        if (b->solo[reps[c]]) continue;  // stepped alone: no tiles
         int best_len = b->len[reps[c]];
         for (int li = 0; li < kNumTileLens; ++li) {
             if (kTileLens[li] == best_len) continue;
@@ -596,6 +673,7 @@ extern "C" int prs_batch_create(const prs_params* runs, int nruns, void* stream,
     b->n.assign(nruns, 0);
     b->cur.assign(nruns, 0);
     b->len.assign(nruns, 16);
+    b->solo.assign(nruns, nullptr);
     b->own_stream = stream == nullptr;
     int rc = PRS_OK;
     if (b->own_stream)
@@ -645,6 +723,8 @@ extern "C" int prs_batch_create(const prs_params* runs, int nruns, void* stream,
     for (int r = 0; r < nruns && !rc; ++r)
         rc = batch_cuda(launch_init_random(b->g[r], PRS_FP32, runs[r].seed, b->phi0[r], b->v[r], true, b->stream),
                         "prs_batch_create");
+    for (int r = 0; r < nruns && !rc; ++r)
+        if (steps_alone(b->g[r])) rc = solo_make(b, r);
     if (!rc) autotune(b);
     for (int r = 0; r < nruns && !rc; ++r) {
         rc = batch_cuda(launch_init_random(b->g[r], PRS_FP32, runs[r].seed, b->phi0[r], b->v[r], true, b->stream),
@@ -675,6 +755,9 @@ extern "C" int prs_batch_run(prs_batch* b, const int64_t* nsteps_per_run, int64_
     Schedule S;
     int rc = run_schedule(b, nsteps_per_run, measure_every, b->group_budget, S, true);
     if (rc) return rc;
+    rc = solo_queue(b, nsteps_per_run, measure_every, S);
+    solo_take_back(b);
+    if (rc) return rc;
     std::vector<DiagAcc> res;
     if (measure_every > 0) {
         size_t nres = 0;
@@ -692,6 +775,10 @@ extern "C" int prs_batch_run(prs_batch* b, const int64_t* nsteps_per_run, int64_
     if ((rc = batch_cuda(cudaMemcpyAsync(b->h_err, b->d_err, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream),
                          "prs_batch_run")))
         return rc;
+    for (prs_sim* s : b->solo)  // the error words of the runs stepped alone
+        if (s && (rc = batch_cuda(cudaMemcpyAsync(&s->h_status->error, &s->d_status->error, sizeof(unsigned),
+                                                  cudaMemcpyDeviceToHost, b->stream), "prs_batch_run")))
+            return rc;
     if ((rc = batch_cuda(cudaStreamSynchronize(b->stream), "prs_batch_run"))) return rc;
     if (b->h_err[0] || b->h_err[1]) {
         record_error("prs_batch_run: a bounded wait in the persistent kernel gave up");
@@ -699,6 +786,8 @@ extern "C" int prs_batch_run(prs_batch* b, const int64_t* nsteps_per_run, int64_
         cudaStreamSynchronize(b->stream);
         return PRS_ETIMEOUT;
     }
+    for (prs_sim* s : b->solo)
+        if (s && (rc = check_device_error(s))) return rc;
     size_t at = 0;
     for (int r = 0; r < R; ++r) {
         const int no = S.runs[r].nout;
@@ -713,7 +802,7 @@ extern "C" int prs_batch_run(prs_batch* b, const int64_t* nsteps_per_run, int64_
         }
         at += no;
         b->n[r] += nsteps_per_run[r];
-        if (nsteps_per_run[r] & 1) b->cur[r] ^= 1;
+        if ((nsteps_per_run[r] & 1) && !b->solo[r]) b->cur[r] ^= 1;
     }
     return PRS_OK;
 }
@@ -751,7 +840,7 @@ extern "C" int prs_batch_set_state(prs_batch* b, int run, const void* h_phi, con
 extern "C" int prs_batch_tuning(prs_batch* b, int run, int* tile_len, double* group_bytes)
 {
     if (!b || run < 0 || run >= (int)b->p.size()) return PRS_EINVAL;
-    if (tile_len) *tile_len = b->len[run];
+    if (tile_len) *tile_len = b->solo[run] ? 0 : b->len[run];
     if (group_bytes) *group_bytes = b->group_budget;
     return PRS_OK;
 }
@@ -760,6 +849,8 @@ extern "C" int prs_batch_destroy(prs_batch* b)
 {
     if (!b) return PRS_EINVAL;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    for (prs_sim* s : b->solo)
+        if (s) prs_destroy(s);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->work);
     cudaFree(b->fields);

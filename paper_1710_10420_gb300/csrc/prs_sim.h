@@ -51,6 +51,11 @@ int cuda_fail(cudaError_t e, const char* what);
 int ensure_buffers(prs_sim* s);
 // After a synchronised read of s->h_status: PRS_ETIMEOUT (once) if a device wait gave up.
 int check_device_error(prs_sim* s);
+// Queue what prs_step_measure does without waiting for it: the Eq. 7/8 sums of the current
+// state into *result (device memory), fused into the first step where a fused kernel serves
+// the box, then nsteps steps through the run's passes.  A bounded wait that gives up sets the
+// run's device error word.
+int step_measure_async(prs_sim* s, int64_t nsteps, DiagAcc* result);
 // PRS_DEBUG: the checks after a call that returned rc (prs_debug.cu); scan_state adds
 // the non-finite scan of the state.  Returns rc when the run has no PRS_DEBUG.
 int debug_after(prs_sim* s, int rc, const char* where, bool scan_state);

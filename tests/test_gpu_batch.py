@@ -198,3 +198,54 @@ def test_production_box_sizes_match_single_runs():
         assert _rel(states[r], phi.astype(np.float64)) <= 1e-6
         del phi
         states[r] = None
+
+
+@pytest.mark.parametrize("ns", [[13, 9, 12], [12, 7, 5]])
+def test_large_runs_are_stepped_alone(ns):
+    """Runs of 2^22 sites or more that the library steps with multi-step passes (here 2D 2048^2,
+    three steps per pass) leave the persistent kernel and are stepped alone per output interval:
+    their outputs and fields are those of the same run stepped by prs_step_measure, bit for bit
+    (the same kernels and reductions), whether the last output falls on a step of the call or
+    not; the small run beside them stays in the persistent kernel and follows a single run."""
+    runs = [((2048, 2048), 1.0, 21), ((256, 128), 2.0, 22), ((2048, 2048), 2.0, 23)]
+    every = 4
+    cap = max(ns) // every + 1
+    b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd in runs])
+    try:
+        assert [prs.prs_batch_tuning(b, r)[0] for r in range(3)][::2] == [0, 0]
+        assert prs.prs_batch_tuning(b, 1)[0] in (4, 8, 16, 32)
+        out = prs.prs_batch_run(b, ns, measure_every=every, out_capacity=cap)
+        states = []
+        for r, (shape, *_rest) in enumerate(runs):
+            phi = np.empty(tuple(reversed(shape)), np.float32)
+            v = np.empty(tuple(reversed(shape)), np.float32)
+            assert prs.prs_batch_get_state(b, r, phi, v) == ns[r]
+            states.append((phi, v))
+        # a second call continues from the state the first left (buffers handed back)
+        out2 = prs.prs_batch_run(b, [3, 2, 4], measure_every=every, out_capacity=cap)
+        phi2 = np.empty((2048, 2048), np.float32)
+        assert prs.prs_batch_get_state(b, 0, phi2, None) == ns[0] + 3
+    finally:
+        prs.prs_batch_destroy(b)
+    for r, (shape, era, seed) in enumerate(runs):
+        sim = prs.Sim(shape, precision=prs.PRS_FP32, era_m=era, seed=seed)
+        sim.init()
+        for k in range(ns[r] // every + 1):
+            left = ns[r] - k * every
+            d = prs.prs_step_measure(sim.handle, min(left, every))
+            assert out[r, k, 0] == every * k == d.step
+            if r != 1:
+                assert out[r, k, 3] == d.n_links and out[r, k, 1] == d.area_per_volume
+                assert out[r, k, 2] == d.gamma_v
+        phi, v, n = sim.get_state()
+        assert n == ns[r]
+        if r != 1:
+            assert np.array_equal(states[r][0], phi) and np.array_equal(states[r][1], v)
+        else:
+            assert _rel(states[r][0], phi.astype(np.float64)) <= 1e-6
+        if r == 0:
+            d = prs.prs_step_measure(sim.handle, 3)
+            assert out2[0, 0, 0] == ns[0] and out2[0, 0, 3] == d.n_links
+            p2, _, _ = sim.get_state()
+            assert np.array_equal(phi2, p2)
+        sim.close()
