@@ -11,6 +11,7 @@
 
 #include "prs.h"
 #include "prs_internal.h"
+#include "prs_runs.h"
 #include "prs_sim.h"
 
 using namespace prs;
@@ -445,12 +446,9 @@ bool prs::cfl_ok_over(const prs_params& p, int64_t n, int64_t nsteps)
     return cfl_ok(p, n) && cfl_ok(p, n + nsteps - 1);
 }
 
-static int prs_step_impl(prs_sim* s, int64_t nsteps)
+// The passes of a call of nsteps (>= 1): n3 of three steps, n2 of two, then n1 single steps.
+static void step_plan(const prs_sim* s, int64_t nsteps, int64_t& n3, int64_t& n2, int64_t& n1)
 {
-    if (!s || nsteps < 0) return PRS_EINVAL;
-    if (!s->initialised) return PRS_ESTATE;
-    if (nsteps == 0) return PRS_OK;
-    if (!cfl_ok_over(s->p, s->n, nsteps)) return PRS_EINVAL;
     const bool repro = (s->p.flags & PRS_REPRO) != 0;
     const int tb = run_tblock(s);
     // Multi-step passes (two or three steps) read dphi across sites, so they write it to a
@@ -467,7 +465,7 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
     // step, else the last pair as two single steps, else the last triple as a pair and a
     // single step.  Single steps otherwise update dphi in place.
     const bool swap_ok = s->owned && (s->p.flags & PRS_DEBUG) == 0;
-    int64_t n3 = 0, n2 = 0, n1 = nsteps;
+    n3 = 0, n2 = 0, n1 = nsteps;
     if (tb == 3) {
         n3 = nsteps / 3;
         n2 = nsteps - 3 * n3 == 2 ? 1 : 0;
@@ -484,6 +482,17 @@ static int prs_step_impl(prs_sim* s, int64_t nsteps)
         else if (n2 > 0) n2 -= 1, n1 += 2;
         else n3 -= 1, n2 += 1, n1 += 1;
     }
+}
+
+static int prs_step_impl(prs_sim* s, int64_t nsteps)
+{
+    if (!s || nsteps < 0) return PRS_EINVAL;
+    if (!s->initialised) return PRS_ESTATE;
+    if (nsteps == 0) return PRS_OK;
+    if (!cfl_ok_over(s->p, s->n, nsteps)) return PRS_EINVAL;
+    const bool repro = (s->p.flags & PRS_REPRO) != 0;
+    int64_t n3, n2, n1;
+    step_plan(s, nsteps, n3, n2, n1);
     unsigned int* err = &s->d_status->error;
     const RunConst<float> rcf{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
                               (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
@@ -649,11 +658,109 @@ static int prs_step_measure_impl(prs_sim* s, int64_t nsteps, prs_diag* out)
     return s->h_status->result.n_nonfinite ? PRS_ENONFINITE : PRS_OK;
 }
 
-int prs::step_measure_async(prs_sim* s, int64_t nsteps, DiagAcc* result)
+int prs::step_runs(prs_sim* const* runs, int nruns, int64_t nsteps)
 {
-    if (!s || !result || nsteps < 0) return PRS_EINVAL;
+    if (nruns < 0 || nsteps < 0) return PRS_EINVAL;
+    if (nruns == 0 || nsteps == 0) return PRS_OK;
+    // the runs qualify when they share their box, stream and plan and the plan's triples are
+    // 2D three-step passes; else each runs alone
+    int64_t n3 = 0, n2 = 0, n1 = 0;
+    bool together = nruns > 1 && nruns <= kT3MaxRuns;
+    for (int r = 0; r < nruns && together; ++r) {
+        const prs_sim* s = runs[r];
+        if (!s) return PRS_EINVAL;
+        if (!s->initialised) return PRS_ESTATE;
+        if (!cfl_ok_over(s->p, s->n, nsteps)) return PRS_EINVAL;
+        int64_t a3, a2, a1;
+        step_plan(s, nsteps, a3, a2, a1);
+        const Geo& g = s->g;
+        const Geo& g0 = runs[0]->g;
+        together = g.dims == 2 && g.nx == g0.nx && g.ny == g0.ny && s->stream == runs[0]->stream &&
+                   s->p.precision == PRS_FP32 && (s->p.flags & PRS_REPRO) == 0 && run_tblock(s) == 3 &&
+                   t3_2d_ok(g) && s->dphi_alt && (r == 0 || (a3 == n3 && a2 == n2 && a1 == n1));
+        if (r == 0) n3 = a3, n2 = a2, n1 = a1;
+    }
+    if (!together || n3 == 0) {
+        for (int r = 0; r < nruns; ++r) {
+            const int rc = prs_step_impl(runs[r], nsteps);
+            if (rc) return rc;
+        }
+        return PRS_OK;
+    }
+    // the passes of prs_step_impl, pass by pass across the runs: the triples as one launch
+    std::vector<int> vi(nruns, 0);  // per run: its vbuf index that holds dphi
+    std::vector<const float*> pin(nruns), vin(nruns);
+    std::vector<float*> pout(nruns), vout(nruns);
+    std::vector<KickF> kk(3 * (size_t)nruns);
+    std::vector<RunConst<float>> rcs(nruns);
+    for (int r = 0; r < nruns; ++r) {
+        const prs_sim* s = runs[r];
+        rcs[r] = RunConst<float>{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
+                                 (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
+    }
+    auto vbuf = [&](int r, int i) { return i == 0 ? runs[r]->dphi : runs[r]->dphi_alt; };
+    int64_t done = 0;
+    for (int64_t k = 0; k < n3; ++k, done += 3) {
+        for (int r = 0; r < nruns; ++r) {
+            prs_sim* s = runs[r];
+            for (int l = 0; l < 3; ++l) {
+                double c[5];
+                step_coefficients(s->p, s->n + done + l, c);
+                kk[3 * (size_t)r + l] = kick_f32(c, s->rc);
+            }
+            pin[r] = (const float*)s->phi[s->cur];
+            pout[r] = (float*)s->phi[1 - s->cur];
+            vin[r] = (const float*)vbuf(r, vi[r]);
+            vout[r] = (float*)vbuf(r, 1 - vi[r]);
+        }
+        const cudaError_t e = launch_step_t3_2d_runs(runs[0]->g, nruns, pin.data(), pout.data(), vin.data(),
+                                                     vout.data(), kk.data(), rcs.data(),
+                                                     &runs[0]->d_status->error, runs[0]->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step_runs launch");
+        for (int r = 0; r < nruns; ++r) runs[r]->cur = 1 - runs[r]->cur, vi[r] = 1 - vi[r];
+    }
+    for (int r = 0; r < nruns; ++r) {
+        prs_sim* s = runs[r];
+        unsigned int* err = &s->d_status->error;
+        int64_t n = s->n + done;
+        for (int64_t k = 0; k < n2; ++k, n += 2) {
+            double a[5], b[5];
+            step_coefficients(s->p, n, a);
+            step_coefficients(s->p, n + 1, b);
+            const cudaError_t e =
+                launch_step_t2(s->g, (const float*)s->phi[s->cur], (float*)s->phi[1 - s->cur],
+                               (const float*)vbuf(r, vi[r]), (float*)vbuf(r, 1 - vi[r]), kick_f32(a, s->rc),
+                               kick_f32(b, s->rc), rcs[r], err, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "step_runs launch");
+            s->cur = 1 - s->cur;
+            vi[r] = 1 - vi[r];
+        }
+        for (int64_t k = 0; k < n1; ++k, ++n) {
+            double c[5];
+            step_coefficients(s->p, n, c);
+            const cudaError_t e = launch_step_io(s->g, s->p.precision, false, s->phi[s->cur], s->phi[1 - s->cur],
+                                                 vbuf(r, vi[r]), s->dphi, &c[0], &c[1], &c[2], 1, s->rc, err,
+                                                 s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "step_runs launch");
+            s->cur = 1 - s->cur;
+            vi[r] = 0;
+        }
+        if (vi[r]) {  // as prs_step_impl: only where the run may swap its dphi buffers
+            void* t = s->dphi;
+            s->dphi = s->dphi_alt;
+            s->dphi_alt = t;
+        }
+        s->n += nsteps;
+    }
+    return PRS_OK;
+}
+
+int prs::step_measure_first(prs_sim* s, int64_t nsteps, DiagAcc* result, int64_t* taken)
+{
+    if (!s || !result || !taken || nsteps < 0) return PRS_EINVAL;
     if (!s->initialised) return PRS_ESTATE;
     if (nsteps > 0 && !cfl_ok_over(s->p, s->n, nsteps)) return PRS_EINVAL;
+    *taken = 0;
     DiagScratch scr = s->scr;
     scr.result = result;
     const RunConst<float> rc{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
@@ -668,9 +775,10 @@ int prs::step_measure_async(prs_sim* s, int64_t nsteps, DiagAcc* result)
         if (e == cudaSuccess) {
             s->cur = 1 - s->cur;
             s->n += 1;
-            return prs_step_impl(s, nsteps - 1);
+            *taken = 1;
+            return PRS_OK;
         }
-        if (e != cudaErrorNotSupported) return cuda_fail(e, "step_measure_async launch");
+        if (e != cudaErrorNotSupported) return cuda_fail(e, "step_measure launch");
     }
     e = cudaErrorNotSupported;
     if (fast_diag_ok(s))
@@ -678,8 +786,8 @@ int prs::step_measure_async(prs_sim* s, int64_t nsteps, DiagAcc* result)
                                 &s->d_status->error, s->stream);
     if (e == cudaErrorNotSupported)
         e = launch_measure(s->g, s->p.precision, s->phi[s->cur], s->dphi, s->rc, scr, s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "step_measure_async launch");
-    return prs_step_impl(s, nsteps);
+    if (e != cudaSuccess) return cuda_fail(e, "step_measure launch");
+    return PRS_OK;
 }
 
 static int prs_measure_ex_impl(prs_sim* s, prs_diag* out)

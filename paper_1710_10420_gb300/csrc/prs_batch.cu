@@ -32,8 +32,11 @@
 //    handle bound to its fields and is stepped after the persistent launch, on the same
 //    stream, per output interval by the fused diagnostics pass and the library's passes,
 //    its outputs written into the same result array: fields and outputs are those of the
-//    run stepped alone through prs_step_measure.  A fixed rule, not a timed choice, so
-//    that two ensembles of the same runs give the same fields.
+//    run stepped alone through prs_step_measure.  Runs of one 2D box at the same step
+//    take their three-step passes together, one launch for up to 16 runs (step_runs), so
+//    that each SM marches a long chunk of rows instead of a short chunk of one run.  A
+//    fixed rule, not a timed choice, so that two ensembles of the same runs give the same
+//    fields.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -46,6 +49,7 @@
 
 #include "prs.h"
 #include "prs_internal.h"
+#include "prs_runs.h"
 #include "prs_reduce.cuh"
 #include "prs_sim.h"
 #include "prs_tile.cuh"
@@ -534,24 +538,49 @@ static int solo_make(prs_batch* b, int r)
     return PRS_OK;
 }
 
-// Queue the runs stepped alone, after the persistent launch: with outputs, per output the
-// diagnostics of the state (into the run's result slot) fused into the first of the steps up
-// to the next output; else the steps.  Leaves b->cur to the caller (solo_take_back).
+// Queue the runs stepped alone, after the persistent launch, in groups of runs of one box
+// at the same step with the same step count (at most kT3MaxRuns a group, which step_runs
+// advances together, pass by pass): with outputs, per output the diagnostics of each run's
+// state (into its result slot) fused into its first step, then the steps up to the next
+// output; else the steps.  Each run gets the passes prs_step_measure would give it alone.
+// Leaves b->cur to the caller (solo_take_back).
 static int solo_queue(prs_batch* b, const int64_t* nsteps, int64_t measure_every, const Schedule& S)
 {
-    for (int r = 0; r < (int)b->p.size(); ++r) {
-        prs_sim* s = b->solo[r];
-        if (!s) continue;
-        solo_sync_in(b, r);
+    const int R = (int)b->p.size();
+    std::vector<char> queued(R, 0);
+    for (int r0 = 0; r0 < R; ++r0) {
+        if (!b->solo[r0] || queued[r0]) continue;
+        std::vector<int> grp;
+        const Geo& a = b->g[r0];
+        for (int r = r0; r < R && (int)grp.size() < kT3MaxRuns; ++r) {
+            const Geo& g = b->g[r];
+            if (b->solo[r] && !queued[r] && g.dims == a.dims && g.nx == a.nx && g.ny == a.ny && g.nz == a.nz &&
+                b->n[r] == b->n[r0] && nsteps[r] == nsteps[r0])
+                grp.push_back(r), queued[r] = 1;
+        }
+        std::vector<prs_sim*> sims;
+        for (int r : grp) {
+            solo_sync_in(b, r);
+            sims.push_back(b->solo[r]);
+        }
+        const int m_runs = (int)sims.size();
         int rc = PRS_OK;
         if (measure_every > 0) {
-            DiagAcc* res = (DiagAcc*)((char*)b->work + S.res_off[r]);
-            for (int k = 0; k < S.runs[r].nout && !rc; ++k) {
-                const int64_t left = nsteps[r] - (int64_t)k * measure_every;
-                rc = step_measure_async(s, left < measure_every ? left : measure_every, res + k);
+            std::vector<int64_t> taken(m_runs, 0);
+            for (int k = 0; k < S.runs[r0].nout && !rc; ++k) {
+                const int64_t left = nsteps[r0] - (int64_t)k * measure_every;
+                const int64_t m = left < measure_every ? left : measure_every;
+                bool same = true;
+                for (int q = 0; q < m_runs && !rc; ++q) {
+                    DiagAcc* res = (DiagAcc*)((char*)b->work + S.res_off[grp[q]]);
+                    rc = step_measure_first(sims[q], m, res + k, &taken[q]);
+                    same = same && taken[q] == taken[0];
+                }
+                if (!rc && same) rc = step_runs(sims.data(), m_runs, m - taken[0]);
+                for (int q = 0; q < m_runs && !rc && !same; ++q) rc = step_runs(&sims[q], 1, m - taken[q]);
             }
         } else {
-            rc = prs_step(s, nsteps[r]);
+            rc = step_runs(sims.data(), m_runs, nsteps[r0]);
         }
         if (rc) return rc;
     }

@@ -51,11 +51,17 @@ int cuda_fail(cudaError_t e, const char* what);
 int ensure_buffers(prs_sim* s);
 // After a synchronised read of s->h_status: PRS_ETIMEOUT (once) if a device wait gave up.
 int check_device_error(prs_sim* s);
-// Queue what prs_step_measure does without waiting for it: the Eq. 7/8 sums of the current
-// state into *result (device memory), fused into the first step where a fused kernel serves
-// the box, then nsteps steps through the run's passes.  A bounded wait that gives up sets the
-// run's device error word.
-int step_measure_async(prs_sim* s, int64_t nsteps, DiagAcc* result);
+// Queue the first part of what prs_step_measure(nsteps) does, without waiting for it: the
+// Eq. 7/8 sums of the current state into *result (device memory), fused into the first step
+// where a fused kernel serves the box.  *taken: the steps queued (1 fused, else 0); the
+// caller steps the other nsteps - *taken as prs_step would, for the same fields.  A bounded
+// wait that gives up sets the run's device error word.
+int step_measure_first(prs_sim* s, int64_t nsteps, DiagAcc* result, int64_t* taken);
+// Step each of several runs by nsteps as prs_step would step it alone (the same passes in the
+// same order, so the same fields), issuing each round of 2D three-step passes as one launch over
+// all the runs when they share a box, stream and plan (at most kT3MaxRuns); else one run after
+// another.
+int step_runs(prs_sim* const* runs, int nruns, int64_t nsteps);
 // PRS_DEBUG: the checks after a call that returned rc (prs_debug.cu); scan_state adds
 // the non-finite scan of the state.  Returns rc when the run has no PRS_DEBUG.
 int debug_after(prs_sim* s, int rc, const char* where, bool scan_state);

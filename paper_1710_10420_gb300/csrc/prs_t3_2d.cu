@@ -14,12 +14,16 @@
 // Only the rows outside the chunk (four at level 1, two at level 2) are computed twice.
 // dphi enters those rows from the neighbouring chunks, so it is read from one buffer and
 // written to another.  At one SM per chunk the two-step pass streams its rows at about the
-// SM's share of the copy bandwidth, so the third level's gain is the bytes it saves.
+// SM's share of the copy bandwidth, so the third level's gain is the bytes it saves.  One
+// launch may also carry up to 16 runs of one box (launch_step_t3_2d_runs), each CTA a chunk
+// of one run.
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "prs_internal.h"
+#include "prs_runs.h"
 #include "prs_ptx.cuh"
 #include "prs_tile.cuh"
 
@@ -65,12 +69,46 @@ __device__ __forceinline__ void row_update(const float* m, const float* c, const
     }
 }
 
-// NX > 0: the row width as a compile-time constant (the 4096-wide production box).
-template <int ITEMS, int NX>
+// The arguments of one run's pass.
+struct T3One {
+    const float* phi_in;
+    float* phi_out;
+    const float* v_in;
+    float* v_out;
+    KickP k[3];
+};
+
+// A: T3One (one run: CTA b takes the rows [b cy, (b+1) cy)) or T3Runs2D (several runs of one
+// box in one launch: CTA b takes chunk b % bpr of run b / bpr, so that a box whose pass alone
+// leaves each SM a short chunk, 2048^2: 14 rows with six of their twenty iterations filling and
+// draining the levels, marches long chunks; chunk boundaries do not change the results, the
+// rows outside a chunk are recomputed from the same inputs).  NX > 0: the row width as a
+// compile-time constant (the 4096-wide production box).  (The body as a device function that
+// both kinds of kernel call compiled to 114 instead of 98 registers for NX = 4096, and the
+// pass ran 25.2 against 22.5 us per step.)
+template <int ITEMS, int NX, class A>
 __global__ void __launch_bounds__(kT3Threads, 1)
-    k_step2d_t3(const float* __restrict__ phi_in, float* __restrict__ phi_out, const float* __restrict__ v_in,
-                float* __restrict__ v_out, int nx_, int ny, int cy, KickP k0, KickP k1, KickP k2, unsigned int* err)
+    k_step2d_t3(const __grid_constant__ A a, int nx_, int ny, int cy, unsigned int* err)
 {
+    constexpr bool kRuns = std::is_same<A, T3Runs2D>::value;
+    int run = 0, blk = blockIdx.x;
+    if constexpr (kRuns) {
+        run = blockIdx.x / a.bpr;
+        blk = blockIdx.x - run * a.bpr;
+        if (blk * cy >= ny) return;  // the whole CTA, before any barrier
+    }
+    const float* __restrict__ phi_in;
+    float* __restrict__ phi_out;
+    const float* __restrict__ v_in;
+    float* __restrict__ v_out;
+    KickP k0, k1, k2;
+    if constexpr (kRuns) {
+        phi_in = a.phi_in[run], phi_out = a.phi_out[run], v_in = a.v_in[run], v_out = a.v_out[run];
+        k0 = a.k[run][0], k1 = a.k[run][1], k2 = a.k[run][2];
+    } else {
+        phi_in = a.phi_in, phi_out = a.phi_out, v_in = a.v_in, v_out = a.v_out;
+        k0 = a.k[0], k1 = a.k[1], k2 = a.k[2];
+    }
     const int nx = NX > 0 ? NX : nx_;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -78,7 +116,7 @@ __global__ void __launch_bounds__(kT3Threads, 1)
     float* ring1 = ring0 + kSlots0 * nx;
     float* ring2 = ring1 + kSlots1 * nx;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int y0 = blockIdx.x * cy;
+    const int y0 = blk * cy;
     const int yn = min(cy, ny - y0);
     const int nq = nx >> 2;
     const int nload = yn + 6;  // level-0 local rows 0 .. yn+5 = global y0-3 .. y0+yn+2
@@ -193,34 +231,58 @@ bool t3_2d_ok(const Geo& g)
     return g.dims == 2 && g.nx % 128 == 0 && g.nx <= 2 * kT3Threads * 4 && g.ny >= 3;
 }
 
+// One launch of the pass for `a` (T3One or T3Runs2D) over `blocks` CTAs of cy rows.
+template <class A>
+static cudaError_t launch_t3_2d(const Geo& g, const A& a, int blocks, int cy, unsigned int* err, cudaStream_t st)
+{
+    static std::atomic<unsigned long long> attr1{0}, attr2{0}, attr4{0};
+    const size_t sm = smem2d_t3(g.nx);
+    cudaError_t e;
+    if (g.nx / 4 > kT3Threads) {
+        e = smem_limit_once(attr2, (const void*)k_step2d_t3<2, 0, A>, (int)smem2d_t3(8 * kT3Threads));
+        if (e == cudaSuccess) e = smem_limit_once(attr4, (const void*)k_step2d_t3<2, 4096, A>, (int)smem2d_t3(4096));
+        if (e != cudaSuccess) return e;
+        if (g.nx == 4096)
+            k_step2d_t3<2, 4096, A><<<blocks, kT3Threads, sm, st>>>(a, g.nx, g.ny, cy, err);
+        else
+            k_step2d_t3<2, 0, A><<<blocks, kT3Threads, sm, st>>>(a, g.nx, g.ny, cy, err);
+    } else {
+        e = smem_limit_once(attr1, (const void*)k_step2d_t3<1, 0, A>, (int)smem2d_t3(4 * kT3Threads));
+        if (e != cudaSuccess) return e;
+        k_step2d_t3<1, 0, A><<<blocks, kT3Threads, sm, st>>>(a, g.nx, g.ny, cy, err);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step_t3_2d(const Geo& g, const float* phi_in, float* phi_out, const float* v_in, float* v_out,
                               KickF k0, KickF k1, KickF k2, RunConst<float> rc, unsigned int* err, cudaStream_t st)
 {
     if (!t3_2d_ok(g)) return cudaErrorNotSupported;
-    const KickP p0 = kick_packed(k0, rc.deta), p1 = kick_packed(k1, rc.deta), p2 = kick_packed(k2, rc.deta);
-    const size_t sm = smem2d_t3(g.nx);
+    const T3One a{phi_in, phi_out, v_in, v_out,
+                  {kick_packed(k0, rc.deta), kick_packed(k1, rc.deta), kick_packed(k2, rc.deta)}};
     const int sms = sm_count_current();
     const int cy = (g.ny + sms - 1) / sms;
-    const int blocks = (g.ny + cy - 1) / cy;
-    static std::atomic<unsigned long long> attr1{0}, attr2{0}, attr4{0};
-    if (g.nx / 4 > kT3Threads) {
-        cudaError_t e = smem_limit_once(attr2, (const void*)k_step2d_t3<2, 0>, (int)smem2d_t3(8 * kT3Threads));
-        if (e != cudaSuccess) return e;
-        e = smem_limit_once(attr4, (const void*)k_step2d_t3<2, 4096>, (int)smem2d_t3(4096));
-        if (e != cudaSuccess) return e;
-        if (g.nx == 4096)
-            k_step2d_t3<2, 4096>
-                <<<blocks, kT3Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, p0, p1, p2, err);
-        else
-            k_step2d_t3<2, 0>
-                <<<blocks, kT3Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, p0, p1, p2, err);
-    } else {
-        const cudaError_t e = smem_limit_once(attr1, (const void*)k_step2d_t3<1, 0>, (int)smem2d_t3(4 * kT3Threads));
-        if (e != cudaSuccess) return e;
-        k_step2d_t3<1, 0>
-            <<<blocks, kT3Threads, sm, st>>>(phi_in, phi_out, v_in, v_out, g.nx, g.ny, cy, p0, p1, p2, err);
+    return launch_t3_2d(g, a, (g.ny + cy - 1) / cy, cy, err, st);
+}
+
+cudaError_t launch_step_t3_2d_runs(const Geo& g, int nruns, const float* const* phi_in, float* const* phi_out,
+                                   const float* const* v_in, float* const* v_out, const KickF* k,
+                                   const RunConst<float>* rc, unsigned int* err, cudaStream_t st)
+{
+    if (!t3_2d_ok(g) || nruns < 1 || nruns > kT3MaxRuns) return cudaErrorNotSupported;
+    T3Runs2D R{};
+    for (int r = 0; r < nruns; ++r) {
+        R.phi_in[r] = phi_in[r];
+        R.phi_out[r] = phi_out[r];
+        R.v_in[r] = v_in[r];
+        R.v_out[r] = v_out[r];
+        for (int l = 0; l < 3; ++l) R.k[r][l] = kick_packed(k[3 * r + l], rc[r].deta);
     }
-    return cudaGetLastError();
+    // chunks per run: the runs' chunks fill the SMs once (one CTA each), every run alike
+    const int sms = sm_count_current();
+    R.bpr = sms / nruns > 0 ? sms / nruns : 1;
+    const int cy = (g.ny + R.bpr - 1) / R.bpr;
+    return launch_t3_2d(g, R, R.bpr * nruns, cy, err, st);
 }
 
 }  // namespace prs

@@ -200,14 +200,18 @@ def test_production_box_sizes_match_single_runs():
         states[r] = None
 
 
-@pytest.mark.parametrize("ns", [[13, 9, 12], [12, 7, 5]])
-def test_large_runs_are_stepped_alone(ns):
-    """Runs of 2^22 sites or more that the library steps with multi-step passes (here 2D 2048^2,
-    three steps per pass) leave the persistent kernel and are stepped alone per output interval:
-    their outputs and fields are those of the same run stepped by prs_step_measure, bit for bit
-    (the same kernels and reductions), whether the last output falls on a step of the call or
-    not; the small run beside them stays in the persistent kernel and follows a single run."""
-    runs = [((2048, 2048), 1.0, 21), ((256, 128), 2.0, 22), ((2048, 2048), 2.0, 23)]
+@pytest.mark.parametrize("big,ns", [((2048, 2048), [13, 9, 12]), ((2048, 2048), [12, 7, 5]),
+                                    ((2048, 2048), [13, 9, 13]), ((2048, 2048), [12, 7, 12]),
+                                    ((4096, 4096), [13, 9, 13])])
+def test_large_runs_are_stepped_alone(big, ns):
+    """Runs of 2^22 sites or more that the library steps with multi-step passes (2D 2048^2 and
+    4096^2, three steps per pass) leave the persistent kernel and are stepped alone per output
+    interval, runs of one box at the same step count together (one launch of the three-step pass
+    for both, different eras); their outputs and fields are those of the same run stepped by
+    prs_step_measure, bit for bit (the same kernels, passes and reductions), whether the last output
+    falls on a step of the call or not; the small run beside them stays in the persistent kernel
+    and follows a single run."""
+    runs = [(big, 1.0, 21), ((256, 128), 2.0, 22), (big, 2.0, 23)]
     every = 4
     cap = max(ns) // every + 1
     b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd in runs])
@@ -222,9 +226,9 @@ def test_large_runs_are_stepped_alone(ns):
             assert prs.prs_batch_get_state(b, r, phi, v) == ns[r]
             states.append((phi, v))
         # a second call continues from the state the first left (buffers handed back)
-        out2 = prs.prs_batch_run(b, [3, 2, 4], measure_every=every, out_capacity=cap)
-        phi2 = np.empty((2048, 2048), np.float32)
-        assert prs.prs_batch_get_state(b, 0, phi2, None) == ns[0] + 3
+        out2 = prs.prs_batch_run(b, [3, 2, 3], measure_every=every, out_capacity=cap)
+        phi2 = np.empty(tuple(reversed(big)), np.float32)
+        assert prs.prs_batch_get_state(b, 2, phi2, None) == ns[2] + 3
     finally:
         prs.prs_batch_destroy(b)
     for r, (shape, era, seed) in enumerate(runs):
@@ -243,9 +247,9 @@ def test_large_runs_are_stepped_alone(ns):
             assert np.array_equal(states[r][0], phi) and np.array_equal(states[r][1], v)
         else:
             assert _rel(states[r][0], phi.astype(np.float64)) <= 1e-6
-        if r == 0:
+        if r == 2:
             d = prs.prs_step_measure(sim.handle, 3)
-            assert out2[0, 0, 0] == ns[0] and out2[0, 0, 3] == d.n_links
+            assert out2[2, 0, 0] == ns[2] and out2[2, 0, 3] == d.n_links and out2[2, 0, 1] == d.area_per_volume
             p2, _, _ = sim.get_state()
             assert np.array_equal(phi2, p2)
         sim.close()
