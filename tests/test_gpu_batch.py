@@ -253,3 +253,36 @@ def test_large_runs_are_stepped_alone(big, ns):
             p2, _, _ = sim.get_state()
             assert np.array_equal(phi2, p2)
         sim.close()
+
+
+@pytest.mark.parametrize("every", [6, 8, 10])
+def test_grouped_passes_follow_the_single_run_plan(every):
+    """Three 2048^2 runs stepped together (one launch per round of three-step passes) through
+    output intervals whose remaining steps plan as a triple and a pair (every 6), two triples and
+    a single step (every 8) and three triples that bound buffers turn into two triples, a pair
+    and a single step (every 10): fields and outputs bit for bit those of each run stepped by
+    prs_step_measure."""
+    runs = [((2048, 2048), 1.0, 31), ((2048, 2048), 2.0, 32), ((2048, 2048), 1.0, 33)]
+    ns = 23
+    cap = ns // every + 1
+    b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd in runs])
+    try:
+        out = prs.prs_batch_run(b, [ns] * 3, measure_every=every, out_capacity=cap)
+        states = []
+        for r in range(3):
+            phi = np.empty((2048, 2048), np.float32)
+            v = np.empty((2048, 2048), np.float32)
+            assert prs.prs_batch_get_state(b, r, phi, v) == ns
+            states.append((phi, v))
+    finally:
+        prs.prs_batch_destroy(b)
+    for r, (shape, era, seed) in enumerate(runs):
+        sim = prs.Sim(shape, precision=prs.PRS_FP32, era_m=era, seed=seed)
+        sim.init()
+        for k in range(ns // every + 1):
+            d = prs.prs_step_measure(sim.handle, min(ns - k * every, every))
+            assert out[r, k, 0] == d.step and out[r, k, 3] == d.n_links
+            assert out[r, k, 1] == d.area_per_volume and out[r, k, 2] == d.gamma_v
+        phi, v, n = sim.get_state()
+        sim.close()
+        assert n == ns and np.array_equal(states[r][0], phi) and np.array_equal(states[r][1], v)
