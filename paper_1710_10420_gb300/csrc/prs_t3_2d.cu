@@ -32,16 +32,31 @@ namespace prs {
 namespace {
 
 constexpr int kT3Threads = 512;
-constexpr int kAhead = 3;            // level-0 rows in flight
-constexpr int kSlots0 = 3 + kAhead;  // level-0 ring rows: three read, kAhead in flight
-constexpr int kSlots1 = 4;           // level-1 ring rows: three read by level 2, one written
-constexpr int kSlots2 = 4;           // level-2 ring rows: three read by level 3, one written
+constexpr int kSlots1 = 4;  // level-1 ring rows: three read by level 2, one written
+constexpr int kSlots2 = 4;  // level-2 ring rows: three read by level 3, one written
 
-size_t smem2d_t3(int nx) { return 128 + (size_t)(kSlots0 + kSlots1 + kSlots2) * nx * sizeof(float); }
+// A CTA's shape: THREADS threads, AHEAD level-0 rows in flight (the level-0 ring holds three
+// read rows and AHEAD in flight), MINB CTAs per SM.  One 512-thread CTA per SM three rows ahead
+// serves a run alone; two 256-thread CTAs per SM two rows ahead (13 rows of rings: 104 KB for
+// 2048-wide rows) serve runs of up to 2048 columns grouped in one launch, whose chunks are long
+// enough for twice as many CTAs, each hiding the other's row latency.
+template <int THREADS, int AHEAD>
+struct T3Shape {
+    static constexpr int kThreads = THREADS, kAhead = AHEAD, kSlots0 = 3 + AHEAD;
+    static constexpr int kMinBlocks = THREADS == kT3Threads ? 1 : 2;
+};
+using T3Alone = T3Shape<kT3Threads, 3>;
+using T3Pair = T3Shape<256, 2>;
 
-static __device__ __noinline__ void drain_rows3(uint64_t* bar, int from, int issued, unsigned int* err)
+template <class SH>
+size_t smem2d_t3(int nx)
 {
-    for (int i = from; i <= issued; ++i) mbar_wait(&bar[i % kSlots0], (unsigned)(i / kSlots0) & 1u, err);
+    return 128 + (size_t)(SH::kSlots0 + kSlots1 + kSlots2) * nx * sizeof(float);
+}
+
+static __device__ __noinline__ void drain_rows3(uint64_t* bar, int from, int issued, int slots, unsigned int* err)
+{
+    for (int i = from; i <= issued; ++i) mbar_wait(&bar[i % slots], (unsigned)(i / slots) & 1u, err);
 }
 
 __device__ __forceinline__ int wrap_row(int y, int ny)
@@ -86,10 +101,11 @@ struct T3One {
 // compile-time constant (the 4096-wide production box).  (The body as a device function that
 // both kinds of kernel call compiled to 114 instead of 98 registers for NX = 4096, and the
 // pass ran 25.2 against 22.5 us per step.)
-template <int ITEMS, int NX, class A>
-__global__ void __launch_bounds__(kT3Threads, 1)
+template <int ITEMS, int NX, class A, class SH = T3Alone>
+__global__ void __launch_bounds__(SH::kThreads, SH::kMinBlocks)
     k_step2d_t3(const __grid_constant__ A a, int nx_, int ny, int cy, unsigned int* err)
 {
+    constexpr int kThreads = SH::kThreads, kAhead = SH::kAhead, kSlots0 = SH::kSlots0;
     constexpr bool kRuns = std::is_same<A, T3Runs2D>::value;
     int run = 0, blk = blockIdx.x;
     if constexpr (kRuns) {
@@ -143,7 +159,7 @@ __global__ void __launch_bounds__(kT3Threads, 1)
     bool on[ITEMS];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        const int q = tid + kT3Threads * j;
+        const int q = tid + kThreads * j;
         on[j] = q < nq;
         col[j] = on[j] ? q : 0;
     }
@@ -167,7 +183,7 @@ __global__ void __launch_bounds__(kT3Threads, 1)
         bool ok = true;
         if (i < nload) ok = mbar_wait(&bar[i % kSlots0], (unsigned)(i / kSlots0) & 1u, err);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) drain_rows3(bar, i, issued, err);
+            if (tid == 0) drain_rows3(bar, i, issued, kSlots0, err);
             return;
         }
         if (tid == 0 && i + kAhead < nload) issue(i + kAhead), issued = i + kAhead;
@@ -236,18 +252,19 @@ template <class A>
 static cudaError_t launch_t3_2d(const Geo& g, const A& a, int blocks, int cy, unsigned int* err, cudaStream_t st)
 {
     static std::atomic<unsigned long long> attr1{0}, attr2{0}, attr4{0};
-    const size_t sm = smem2d_t3(g.nx);
+    const size_t sm = smem2d_t3<T3Alone>(g.nx);
     cudaError_t e;
     if (g.nx / 4 > kT3Threads) {
-        e = smem_limit_once(attr2, (const void*)k_step2d_t3<2, 0, A>, (int)smem2d_t3(8 * kT3Threads));
-        if (e == cudaSuccess) e = smem_limit_once(attr4, (const void*)k_step2d_t3<2, 4096, A>, (int)smem2d_t3(4096));
+        e = smem_limit_once(attr2, (const void*)k_step2d_t3<2, 0, A>, (int)smem2d_t3<T3Alone>(8 * kT3Threads));
+        if (e == cudaSuccess)
+            e = smem_limit_once(attr4, (const void*)k_step2d_t3<2, 4096, A>, (int)smem2d_t3<T3Alone>(4096));
         if (e != cudaSuccess) return e;
         if (g.nx == 4096)
             k_step2d_t3<2, 4096, A><<<blocks, kT3Threads, sm, st>>>(a, g.nx, g.ny, cy, err);
         else
             k_step2d_t3<2, 0, A><<<blocks, kT3Threads, sm, st>>>(a, g.nx, g.ny, cy, err);
     } else {
-        e = smem_limit_once(attr1, (const void*)k_step2d_t3<1, 0, A>, (int)smem2d_t3(4 * kT3Threads));
+        e = smem_limit_once(attr1, (const void*)k_step2d_t3<1, 0, A>, (int)smem2d_t3<T3Alone>(4 * kT3Threads));
         if (e != cudaSuccess) return e;
         k_step2d_t3<1, 0, A><<<blocks, kT3Threads, sm, st>>>(a, g.nx, g.ny, cy, err);
     }
@@ -278,11 +295,34 @@ cudaError_t launch_step_t3_2d_runs(const Geo& g, int nruns, const float* const* 
         R.v_out[r] = v_out[r];
         for (int l = 0; l < 3; ++l) R.k[r][l] = kick_packed(k[3 * r + l], rc[r].deta);
     }
-    // chunks per run: the runs' chunks fill the SMs once (one CTA each), every run alike
     const int sms = sm_count_current();
-    R.bpr = sms / nruns > 0 ? sms / nruns : 1;
+    if (g.nx > 8 * T3Pair::kThreads) {  // 4096-wide rows: one 512-thread CTA per SM
+        R.bpr = sms / nruns > 0 ? sms / nruns : 1;
+        const int cy = (g.ny + R.bpr - 1) / R.bpr;
+        return launch_t3_2d(g, R, R.bpr * nruns, cy, err, st);
+    }
+    // up to 2048 columns: 256-thread CTAs, two per SM; the runs' chunks fill the CTA slots once
+    const void* fn = g.nx > 4 * T3Pair::kThreads ? (const void*)k_step2d_t3<2, 0, T3Runs2D, T3Pair>
+                                                 : (const void*)k_step2d_t3<1, 0, T3Runs2D, T3Pair>;
+    static std::atomic<unsigned long long> attr_p1{0}, attr_p2{0};
+    const size_t sm = smem2d_t3<T3Pair>(g.nx);
+    cudaError_t e = smem_limit_once(g.nx > 4 * T3Pair::kThreads ? attr_p2 : attr_p1, fn,
+                                    (int)smem2d_t3<T3Pair>(8 * T3Pair::kThreads));
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T3Pair::kThreads, sm) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int slots = per_sm * sms;
+    R.bpr = slots / nruns > 0 ? slots / nruns : 1;
     const int cy = (g.ny + R.bpr - 1) / R.bpr;
-    return launch_t3_2d(g, R, R.bpr * nruns, cy, err, st);
+    if (g.nx > 4 * T3Pair::kThreads)
+        k_step2d_t3<2, 0, T3Runs2D, T3Pair><<<R.bpr * nruns, T3Pair::kThreads, sm, st>>>(R, g.nx, g.ny, cy, err);
+    else
+        k_step2d_t3<1, 0, T3Runs2D, T3Pair><<<R.bpr * nruns, T3Pair::kThreads, sm, st>>>(R, g.nx, g.ny, cy, err);
+    return cudaGetLastError();
 }
 
 }  // namespace prs
