@@ -275,9 +275,11 @@ int prs_destroy(prs_sim* sim);
 /* Create an ensemble of nruns runs (each validated as by prs_create), allocate all
  * fields, pick a tile length for each geometry class of runs (4 to 32 planes or bands)
  * and the L2 grouping by timing short trials on them (the autotuner), then set every
- * run to its seeded random initial condition (step 0).  A run of 2^22 sites or more
- * that the library steps with multi-step passes (prs_default_tblock >= 2) fills the
- * GPU by itself: it is stepped alone, after the persistent launch of the others, as
+ * run to its seeded random initial condition (step 0).  A run that the library steps
+ * with multi-step passes (prs_default_tblock >= 2) and whose box has 2^22 sites or more
+ * (it fills the GPU by itself), or, in 2D, 2^20 sites or more in rows of at least 1024
+ * columns with at least 8 runs of that box in the ensemble (their passes are launched
+ * together), is stepped alone, after the persistent launch of the others, as
  * prs_step_measure would step it (its fields and outputs are those of the same run
  * stepped alone; the run holds a second dphi buffer like a prs_sim).  stream may be
  * NULL (the ensemble then creates its own stream). */

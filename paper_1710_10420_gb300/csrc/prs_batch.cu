@@ -24,8 +24,9 @@
 //    candidates at creation (the autotuner).  The persistent launch is captured
 //    once into a CUDA graph and replayed while the step counts stay the same; the
 //    counters are reset and the per-step coefficients uploaded before each replay.
-//  * Runs stepped alone: a run whose box fills the GPU by itself (2^22 sites or more)
-//    and that the library steps with multi-step passes stays out of the persistent
+//  * Runs stepped alone: a run whose box fills the GPU by itself (2^22 sites or more),
+//    or a 2D run of 2^20 sites or more with 1024-column rows among at least 8 runs of
+//    its box, that the library steps with multi-step passes stays out of the persistent
 //    kernel.  It gains nothing from sharing the GPU, and its multi-step passes move a
 //    half or a third of the bytes of one-step items (2048^2: 9.4 us per step with three
 //    steps per pass against 11.4 us as one-step items).  Such a run gets a single-run
@@ -505,11 +506,17 @@ static int run_schedule(prs_batch* b, const int64_t* nsteps, int64_t measure_eve
     return batch_cuda(cudaGetLastError(), "batch launch");
 }
 
-// Runs stepped alone: boxes of 2^22 sites or more that the library steps with multi-step
-// passes (the ensemble's runs are FP32).
-static bool steps_alone(const Geo& g)
+// Runs stepped alone, among those the library steps with multi-step passes (the ensemble's
+// runs are FP32): boxes of 2^22 sites or more, which fill the GPU by themselves, and 2D boxes
+// of 2^20 sites or more with rows of at least 1024 columns when the ensemble holds at least 8
+// runs of that box, whose grouped three-step launches fill it together (16 x 1024^2 in the
+// 64-run ensemble: 1.41 s against 1.47-1.60 s with them in the persistent kernel).
+// class_runs: the runs of this box in the ensemble.
+static bool steps_alone(const Geo& g, int class_runs)
 {
-    return g.S >= ((int64_t)1 << 22) && default_fused_steps(g, PRS_FP32, false) >= 2;
+    if (default_fused_steps(g, PRS_FP32, false) < 2) return false;
+    if (g.S >= ((int64_t)1 << 22)) return true;
+    return g.dims == 2 && g.nx >= 1024 && g.S >= ((int64_t)1 << 20) && class_runs >= 8;
 }
 
 // A run stepped alone: its handle follows the batch's view of the run (which field buffer
@@ -752,8 +759,12 @@ extern "C" int prs_batch_create(const prs_params* runs, int nruns, void* stream,
     for (int r = 0; r < nruns && !rc; ++r)
         rc = batch_cuda(launch_init_random(b->g[r], PRS_FP32, runs[r].seed, b->phi0[r], b->v[r], true, b->stream),
                         "prs_batch_create");
-    for (int r = 0; r < nruns && !rc; ++r)
-        if (steps_alone(b->g[r])) rc = solo_make(b, r);
+    for (int r = 0; r < nruns && !rc; ++r) {
+        int same = 0;
+        for (const Geo& q : b->g)
+            same += q.dims == b->g[r].dims && q.nx == b->g[r].nx && q.ny == b->g[r].ny && q.nz == b->g[r].nz;
+        if (steps_alone(b->g[r], same)) rc = solo_make(b, r);
+    }
     if (!rc) autotune(b);
     for (int r = 0; r < nruns && !rc; ++r) {
         rc = batch_cuda(launch_init_random(b->g[r], PRS_FP32, runs[r].seed, b->phi0[r], b->v[r], true, b->stream),

@@ -286,3 +286,41 @@ def test_grouped_passes_follow_the_single_run_plan(every):
         phi, v, n = sim.get_state()
         sim.close()
         assert n == ns and np.array_equal(states[r][0], phi) and np.array_equal(states[r][1], v)
+
+
+@pytest.mark.parametrize("n1024", [8, 7])
+def test_classes_of_1024_rows_go_alone_in_numbers(n1024):
+    """2D runs of 1024^2 (2^20 sites, rows of 1024 columns) are stepped alone, their three-step
+    passes launched together, when the ensemble holds at least 8 of them; with 7 they stay in the
+    persistent kernel.  Either way each run's fields follow the run stepped alone (bit for bit when
+    stepped alone, to FP32 rounding in the persistent kernel)."""
+    runs = [((1024, 1024), 1.0 + (i & 1), 40 + i) for i in range(n1024)] + [((256, 128), 2.0, 60)]
+    ns, every = 11, 5
+    b = prs.prs_batch_create([_params(s, e, sd) for s, e, sd in runs])
+    try:
+        tl = [prs.prs_batch_tuning(b, r)[0] for r in range(len(runs))]
+        alone = n1024 >= 8
+        assert all((t == 0) == alone for t in tl[:-1]) and tl[-1] in (4, 8, 16, 32)
+        out = prs.prs_batch_run(b, [ns] * len(runs), measure_every=every, out_capacity=ns // every + 1)
+        states = []
+        for r, (shape, *_rest) in enumerate(runs):
+            phi = np.empty(tuple(reversed(shape)), np.float32)
+            assert prs.prs_batch_get_state(b, r, phi, None) == ns
+            states.append(phi)
+    finally:
+        prs.prs_batch_destroy(b)
+    for r in (0, 1, n1024 - 1):
+        shape, era, seed = runs[r]
+        sim = prs.Sim(shape, precision=prs.PRS_FP32, era_m=era, seed=seed)
+        sim.init()
+        for k in range(ns // every + 1):
+            d = prs.prs_step_measure(sim.handle, min(ns - k * every, every))
+            assert out[r, k, 0] == d.step
+            if alone:
+                assert out[r, k, 3] == d.n_links and out[r, k, 1] == d.area_per_volume
+        phi, _, _ = sim.get_state()
+        sim.close()
+        if alone:
+            assert np.array_equal(states[r], phi)
+        else:
+            assert _rel(states[r], phi.astype(np.float64)) <= 1e-6
