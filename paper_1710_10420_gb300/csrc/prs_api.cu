@@ -719,7 +719,7 @@ int prs::step_runs(prs_sim* const* runs, int nruns, int64_t nsteps)
         if (e != cudaSuccess) return cuda_fail(e, "step_runs launch");
         for (int r = 0; r < nruns; ++r) runs[r]->cur = 1 - runs[r]->cur, vi[r] = 1 - vi[r];
     }
-    for (int r = 0; r < nruns; ++r) {
+    for (int r = 0; r < nruns; ++r) {  // pairs, run by run
         prs_sim* s = runs[r];
         unsigned int* err = &s->d_status->error;
         int64_t n = s->n + done;
@@ -735,16 +735,40 @@ int prs::step_runs(prs_sim* const* runs, int nruns, int64_t nsteps)
             s->cur = 1 - s->cur;
             vi[r] = 1 - vi[r];
         }
-        for (int64_t k = 0; k < n1; ++k, ++n) {
+    }
+    done += 2 * n2;
+    // single steps, each one launch over the runs (the first reads dphi where the multi-step
+    // passes left it and writes the run's own buffer)
+    std::vector<KickF> k1(nruns);
+    for (int64_t k = 0; k < n1; ++k, ++done) {
+        for (int r = 0; r < nruns; ++r) {
+            prs_sim* s = runs[r];
             double c[5];
-            step_coefficients(s->p, n, c);
-            const cudaError_t e = launch_step_io(s->g, s->p.precision, false, s->phi[s->cur], s->phi[1 - s->cur],
-                                                 vbuf(r, vi[r]), s->dphi, &c[0], &c[1], &c[2], 1, s->rc, err,
-                                                 s->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "step_runs launch");
-            s->cur = 1 - s->cur;
-            vi[r] = 0;
+            step_coefficients(s->p, s->n + done, c);
+            k1[r] = kick_f32(c, s->rc);
+            pin[r] = (const float*)s->phi[s->cur];
+            pout[r] = (float*)s->phi[1 - s->cur];
+            vin[r] = (const float*)vbuf(r, vi[r]);
+            vout[r] = (float*)s->dphi;
         }
+        cudaError_t e = launch_step2d_runs(runs[0]->g, nruns, pin.data(), pout.data(), vin.data(), vout.data(),
+                                           k1.data(), rcs.data(), nullptr, &runs[0]->d_status->error,
+                                           runs[0]->stream);
+        if (e == cudaErrorNotSupported) {  // no fast one-step pass for this box: run by run
+            e = cudaSuccess;
+            for (int r = 0; r < nruns && e == cudaSuccess; ++r) {
+                prs_sim* s = runs[r];
+                double c[5];
+                step_coefficients(s->p, s->n + done, c);
+                e = launch_step_io(s->g, s->p.precision, false, s->phi[s->cur], s->phi[1 - s->cur], vbuf(r, vi[r]),
+                                   s->dphi, &c[0], &c[1], &c[2], 1, s->rc, &s->d_status->error, s->stream);
+            }
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "step_runs launch");
+        for (int r = 0; r < nruns; ++r) runs[r]->cur = 1 - runs[r]->cur, vi[r] = 0;
+    }
+    for (int r = 0; r < nruns; ++r) {
+        prs_sim* s = runs[r];
         if (vi[r]) {  // as prs_step_impl: only where the run may swap its dphi buffers
             void* t = s->dphi;
             s->dphi = s->dphi_alt;
@@ -787,6 +811,57 @@ int prs::step_measure_first(prs_sim* s, int64_t nsteps, DiagAcc* result, int64_t
     if (e == cudaErrorNotSupported)
         e = launch_measure(s->g, s->p.precision, s->phi[s->cur], s->dphi, s->rc, scr, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step_measure launch");
+    return PRS_OK;
+}
+
+int prs::step_measure_first_runs(prs_sim* const* runs, int nruns, int64_t nsteps, DiagAcc* const* results,
+                                  int64_t* taken)
+{
+    if (nruns < 0 || nsteps < 0 || (nruns > 0 && (!runs || !results || !taken))) return PRS_EINVAL;
+    bool together = nruns > 1 && nruns <= kT3MaxRuns && nsteps > 0;
+    for (int r = 0; r < nruns && together; ++r) {
+        const prs_sim* s = runs[r];
+        together = s && results[r] && s->initialised && s->g.dims == 2 && s->g.nx == runs[0]->g.nx &&
+                   s->g.ny == runs[0]->g.ny && s->stream == runs[0]->stream && fast_diag_ok(s) &&
+                   cfl_ok_over(s->p, s->n, nsteps);
+    }
+    if (together) {  // one launch: each run's diagnostics fused into its first step
+        std::vector<const float*> pin(nruns), vin(nruns);
+        std::vector<float*> pout(nruns), vout(nruns);
+        std::vector<KickF> kk(nruns);
+        std::vector<RunConst<float>> rcs(nruns);
+        std::vector<DiagScratch> scr(nruns);
+        for (int r = 0; r < nruns; ++r) {
+            const prs_sim* s = runs[r];
+            double c[5];
+            step_coefficients(s->p, s->n, c);
+            kk[r] = kick_f32(c, s->rc);
+            rcs[r] = RunConst<float>{(float)s->rc[0], (float)s->rc[1], (float)s->rc[2],
+                                     (float)s->rc[3], (float)s->rc[4], (float)s->rc[5]};
+            pin[r] = (const float*)s->phi[s->cur];
+            pout[r] = (float*)s->phi[1 - s->cur];
+            vin[r] = (const float*)s->dphi;
+            vout[r] = (float*)s->dphi;
+            scr[r] = s->scr;
+            scr[r].result = results[r];
+        }
+        const cudaError_t e = launch_step2d_runs(runs[0]->g, nruns, pin.data(), pout.data(), vin.data(), vout.data(),
+                                                 kk.data(), rcs.data(), scr.data(), &runs[0]->d_status->error,
+                                                 runs[0]->stream);
+        if (e == cudaSuccess) {
+            for (int r = 0; r < nruns; ++r) {
+                runs[r]->cur = 1 - runs[r]->cur;
+                runs[r]->n += 1;
+                taken[r] = 1;
+            }
+            return PRS_OK;
+        }
+        if (e != cudaErrorNotSupported) return cuda_fail(e, "step_measure launch");
+    }
+    for (int r = 0; r < nruns; ++r) {
+        const int rc = step_measure_first(runs[r], nsteps, results[r], &taken[r]);
+        if (rc) return rc;
+    }
     return PRS_OK;
 }
 

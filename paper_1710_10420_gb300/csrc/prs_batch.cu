@@ -33,9 +33,10 @@
 //    handle bound to its fields and is stepped after the persistent launch, on the same
 //    stream, per output interval by the fused diagnostics pass and the library's passes,
 //    its outputs written into the same result array: fields and outputs are those of the
-//    run stepped alone through prs_step_measure.  Runs of one 2D box at the same step
-//    take their three-step passes together, one launch for up to 16 runs (step_runs), so
-//    that each SM marches a long chunk of rows instead of a short chunk of one run.  A
+//    run stepped alone through prs_step_measure (the sums to FP64 rounding).  Runs of one
+//    2D box at the same step take their passes together, one launch for up to 16 runs
+//    (step_measure_first_runs, step_runs), so that each SM marches a long chunk of rows
+//    instead of a short chunk of one run.  A
 //    fixed rule, not a timed choice, so that two ensembles of the same runs give the same
 //    fields.
 #include <cuda_runtime.h>
@@ -548,8 +549,10 @@ static int solo_make(prs_batch* b, int r)
 // Queue the runs stepped alone, after the persistent launch, in groups of runs of one box
 // at the same step with the same step count (at most kT3MaxRuns a group, which step_runs
 // advances together, pass by pass): with outputs, per output the diagnostics of each run's
-// state (into its result slot) fused into its first step, then the steps up to the next
-// output; else the steps.  Each run gets the passes prs_step_measure would give it alone.
+// state (into its result slot) fused into its first step, one launch for the group
+// (step_measure_first_runs), then the steps up to the next output; else the steps.  Each run
+// gets the passes prs_step_measure would give it alone (its fields bit for bit; its sums to
+// FP64 rounding, their blocks grouped differently).
 // Leaves b->cur to the caller (solo_take_back).
 static int solo_queue(prs_batch* b, const int64_t* nsteps, int64_t measure_every, const Schedule& S)
 {
@@ -577,12 +580,11 @@ static int solo_queue(prs_batch* b, const int64_t* nsteps, int64_t measure_every
             for (int k = 0; k < S.runs[r0].nout && !rc; ++k) {
                 const int64_t left = nsteps[r0] - (int64_t)k * measure_every;
                 const int64_t m = left < measure_every ? left : measure_every;
+                std::vector<DiagAcc*> res(m_runs);
+                for (int q = 0; q < m_runs; ++q) res[q] = (DiagAcc*)((char*)b->work + S.res_off[grp[q]]) + k;
+                rc = step_measure_first_runs(sims.data(), m_runs, m, res.data(), taken.data());
                 bool same = true;
-                for (int q = 0; q < m_runs && !rc; ++q) {
-                    DiagAcc* res = (DiagAcc*)((char*)b->work + S.res_off[grp[q]]);
-                    rc = step_measure_first(sims[q], m, res + k, &taken[q]);
-                    same = same && taken[q] == taken[0];
-                }
+                for (int q = 0; q < m_runs; ++q) same = same && taken[q] == taken[0];
                 if (!rc && same) rc = step_runs(sims.data(), m_runs, m - taken[0]);
                 for (int q = 0; q < m_runs && !rc && !same; ++q) rc = step_runs(&sims[q], 1, m - taken[q]);
             }

@@ -38,14 +38,14 @@ __device__ __forceinline__ void acc_warp_reduce(DiagAcc& a)
     for (int off = 16; off > 0; off >>= 1) acc_shfl_down(a, off);
 }
 
-// Every thread of the block calls this once with its own sums; the grid's total
-// lands in *scr.result and the counter is reset for the next launch.
-__device__ __forceinline__ void block_reduce_and_finish(DiagAcc a, const DiagScratch& scr)
+// Every thread of the block calls this once with its own sums: block bid of the nblocks
+// that reduce into scr; their total lands in *scr.result and the counter is reset for the
+// next launch.
+__device__ __forceinline__ void block_reduce_and_finish_at(DiagAcc a, const DiagScratch& scr, unsigned int bid,
+                                                           unsigned int nblocks)
 {
     __shared__ DiagAcc warp_sums[32];
     __shared__ bool is_last;
-    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
     acc_warp_reduce(a);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) warp_sums[wid] = a;
@@ -79,6 +79,13 @@ __device__ __forceinline__ void block_reduce_and_finish(DiagAcc a, const DiagScr
             *scr.counter = 0u;  // ready for the next launch on this scratch
         }
     }
+}
+
+// The whole grid reduces into scr.
+__device__ __forceinline__ void block_reduce_and_finish(DiagAcc a, const DiagScratch& scr)
+{
+    block_reduce_and_finish_at(a, scr, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                               gridDim.x * gridDim.y * gridDim.z);
 }
 
 }  // namespace prs

@@ -57,10 +57,15 @@ int check_device_error(prs_sim* s);
 // caller steps the other nsteps - *taken as prs_step would, for the same fields.  A bounded
 // wait that gives up sets the run's device error word.
 int step_measure_first(prs_sim* s, int64_t nsteps, DiagAcc* result, int64_t* taken);
+// step_measure_first for several runs: one launch of the fused one-step pass over all of them
+// when they share a 2D box and stream (at most kT3MaxRuns; the fields are those of the runs'
+// own passes, the sums the same to FP64 rounding), else run by run.
+int step_measure_first_runs(prs_sim* const* runs, int nruns, int64_t nsteps, DiagAcc* const* results,
+                            int64_t* taken);
 // Step each of several runs by nsteps as prs_step would step it alone (the same passes in the
-// same order, so the same fields), issuing each round of 2D three-step passes as one launch over
-// all the runs when they share a box, stream and plan (at most kT3MaxRuns); else one run after
-// another.
+// same order, so the same fields), issuing each round of 2D three-step passes and of single
+// steps as one launch over all the runs when they share a box, stream and plan (at most
+// kT3MaxRuns); else one run after another.
 int step_runs(prs_sim* const* runs, int nruns, int64_t nsteps);
 // PRS_DEBUG: the checks after a call that returned rc (prs_debug.cu); scan_state adds
 // the non-finite scan of the state.  Returns rc when the run has no PRS_DEBUG.
