@@ -589,8 +589,9 @@ def run_batch_figure(prs, stream, dev, scale: float) -> dict:
             "site_updates": total, "batched_s": ms_batch / 1e3, "one_at_a_time_s": ms_seq / 1e3,
             "batched_value": total / (ms_batch / 1e3), "one_at_a_time_value": total / (ms_seq / 1e3),
             "unit": "site-updates/s", "speedup": ms_seq / ms_batch, "create_s": t_create,
-            "tuned_tile_len": tl, "tile_len_0": "a class of boxes stepped alone (2^22 sites and more, multi-step "
-            "passes), after the persistent launch of the others", "tuned_group_bytes": budget,
+            "tuned_tile_len": tl, "tile_len_0": "a class of boxes stepped alone after the persistent launch of the others, "
+            "each pass launched once for up to 16 runs of the box (boxes of 2^22 sites and more, or 2D "
+            "classes of 8+ runs with 1024-column rows; multi-step passes)", "tuned_group_bytes": budget,
             "first_output_run0": list(out[0, 0])}
 
 
